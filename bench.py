@@ -1,0 +1,327 @@
+"""Benchmark: DOF/s of the optimized Schwarz gravimetry solve on one GB300.
+
+One step = one full Schwarz solve (Robin RHS, batched subdomain Jacobi-PCG,
+Robin exchange, global residual -- every step of the hot path) from u = 0
+to a relative residual of 1e-8 on the 64^3 layered workload (unit cube, Q2,
+4 x 4 x 4 subdomains, 2,048,383 unknowns).  The subdomain matrices (1.6 GB
+of SELL data) are larger than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun with N > 1 every rank solves
+its own replica of the workload (the solve does not shard: replicas only);
+the value is the units of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DOF/s solved to 1e-8 rel residual, mixed vs FP64; SpMV GB/s vs HBM peak"
+WORKLOAD = "layered64"
+P_ROBIN = 20.0
+RTOL = 1e-8
+INNER_RTOL = 1e-10
+FALLBACK_HBM = 6800.0
+
+
+def _workload_desc(prob, p):
+    return (f"{WORKLOAD}: unit cube, Q2 {prob.nx}^3 elements ({prob.n_dofs:,} unknowns), "
+            f"{len(prob.cx)-1}x{len(prob.cy)-1}x{len(prob.cz)-1} subdomains, 3 density layers + "
+            f"20 random spheres (seed 0), Robin p={p:g}, subdomain PCG to {INNER_RTOL:g}, "
+            f"Schwarz to {RTOL:g}")
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for name in ("osm_kernels.cu", "osm_internal.h"):
+        with open(os.path.join(ROOT, "paper_2112_03851_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_per_launch(n_local):
+    """DRAM bytes per SpMV launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "spmv_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("kernel_hash") != _kernel_hash():
+            return None
+        return float(d["bytes_per_row"]) * n_local
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return None
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_baseline(prob, p, n_outer_needed, budget_s=20.0):
+    """The oracle's sequential Schwarz (OpenMP over subdomains) on the same
+    workload: time a bounded number of Schwarz iterations, scale to the
+    iterations the solve needs."""
+    threads = os.cpu_count() or 1
+    os.environ.setdefault("OMP_NUM_THREADS", str(threads))
+    threads = int(os.environ["OMP_NUM_THREADS"])
+    import oracle
+    t0 = time.perf_counter()
+    S = oracle.Schwarz.from_problem(prob, p=p)
+    setup = time.perf_counter() - t0
+    done, t_iter = 0, 0.0
+    while done < n_outer_needed and (t_iter < budget_s or done == 0):
+        t = time.perf_counter()
+        S.iterate(inner_rtol=INNER_RTOL)
+        t_iter += time.perf_counter() - t
+        done += 1
+    per_iter = t_iter / done
+    value = prob.n_dofs / (per_iter * n_outer_needed)
+    return {"value": value, "unit": "DOF/s", "cores": threads, "kind": "oracle",
+            "sample": (f"{done} of {n_outer_needed} Schwarz iterations of the FP64 oracle on {WORKLOAD} "
+                       f"({per_iter:.2f} s each, OpenMP over subdomains; setup {setup:.1f} s excluded), "
+                       f"solve time extrapolated to {n_outer_needed} iterations")}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import gen
+    prob = gen.workload(WORKLOAD)
+    n_outer = _reference_iterations()
+    threads = int(os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1)))
+    import oracle
+    S = oracle.Schwarz.from_problem(prob, p=P_ROBIN)
+    for _ in range(args.warmup):
+        S.iterate(inner_rtol=INNER_RTOL)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        S.iterate(inner_rtol=INNER_RTOL)
+        times.append(time.perf_counter() - t)
+    per_iter = sum(times) / len(times)
+    value = prob.n_dofs / (per_iter * n_outer)
+    sample = (f"each step: one Schwarz iteration of the FP64 oracle on {WORKLOAD} (OpenMP over "
+              f"subdomains); DOF/s = unknowns / (mean step time x {n_outer} iterations to {RTOL:g})")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": _workload_desc(prob, P_ROBIN)},
+            "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _reference_iterations():
+    path = os.path.join(ROOT, "tests", "golden", "layered64_iterations.json")
+    try:
+        with open(path) as f:
+            return int(json.load(f)["schwarz_iterations"])
+    except Exception:
+        return 150
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import gen
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2112_03851_gb300 as pkg
+    try:
+        pkg.load()
+    except ImportError:
+        from paper_2112_03851_gb300 import build as b
+        b.build()
+        pkg.load()
+
+    prob = gen.workload(WORKLOAD)
+    stream = torch.cuda.current_stream()
+    sol = pkg.Solver.from_problem(prob, p=P_ROBIN, inner_rtol=INNER_RTOL, max_outer=5000)
+    phi = torch.zeros(sol.info["n_nodes"], dtype=torch.float64, device="cuda")
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    for _ in range(max(args.warmup, 1)):
+        sol.solve(RTOL, phi=phi)
+    st = sol.stats()
+    n_outer, n_cg = st["n_outer"], st["n_cg_steps"]
+    launches_per_step = st["n_launches"]
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        launches = 0
+        for _ in range(args.steps):
+            _, it, rel = sol.solve(RTOL, phi=phi)
+            launches += sol.stats()["n_launches"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    clocks = clk.summary()
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = ws * prob.n_dofs / (ms_max / 1e3)
+
+    # end to end through the public API from host buffers: new density in,
+    # solution out to pinned host memory, every step
+    phi_host = torch.empty(sol.info["n_nodes"], dtype=torch.float64, pin_memory=True)
+    drho = np.ascontiguousarray(prob.drho)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sol.set_density(drho)
+        sol.solve(RTOL, phi=phi)
+        phi_host.copy_(phi, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+    e2e = {"value": ws * prob.n_dofs / float(te.item()), "unit": "DOF/s",
+           "h2d_bytes_per_step": 2 * sol.info["vec_rows"] * 8,   # load vector f and b
+           "d2h_bytes_per_step": sol.info["n_nodes"] * 8}        # phi
+
+    # roofline of the dominant kernel (batched SELL SpMV), CUDA events
+    spmv_ms = sol.profile_spmv(20)
+    spmv_bytes = sol.spmv_bytes()
+    peak, peak_kind = _peaks()
+    achieved = spmv_bytes / (spmv_ms / 1e3) / 1e9
+    traffic = _traffic_per_launch(sol.info["n_local"])
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "k_spmv (batched SELL-32 FP64 SpMV, all 64 subdomains)",
+                "peak_kind": f"{peak_kind} hbm_gbs (copy)", "ms_per_launch": round(spmv_ms, 5),
+                "algorithmic_bytes": spmv_bytes}
+
+    line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": _workload_desc(prob, P_ROBIN),
+                       "l2": "inputs larger than L2 (1.6 GB of subdomain matrices), no flush",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
+            "gpu_launches": int(launches),
+            "schwarz_iterations": n_outer, "cg_steps_per_solve": n_cg,
+            "launches_per_step": int(launches_per_step),
+            "setup_s": round(sol.info["setup_seconds"], 2),
+            "e2e": e2e, "roofline": roofline, "clocks": clocks}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(prob, P_ROBIN, n_outer)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

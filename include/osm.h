@@ -1,0 +1,250 @@
+/*
+ * osm.h -- C ABI of the GB300 optimized-Schwarz gravimetry library (libosm.so).
+ *
+ * The library solves the gravimetry Poisson problem of Sec. 2,
+ *     -Laplace(Phi) = 4 pi G drho   in a box,  Phi = 0 on its boundary,
+ * discretised by Q2 (27-node triquadratic) hexahedral finite elements
+ * ("high order finite elements", Sec. 6), with the non-overlapping optimized
+ * Schwarz method of Sec. 3 using the zeroth-order Robin transmission operator
+ * A = p ("oo0"): every iteration solves all subdomain problems
+ *     (K_i + p_i M_Gi) u_i = f_i + sum_j lam_ij
+ * by Jacobi-preconditioned CG (Sec. 6), all subdomains batched in the same
+ * kernels, then exchanges the interface Robin data
+ *     lam_ij <- (p_i + p_j) M_Gij u_j - lam_ji
+ * and evaluates the global relative residual ||f - K ubar|| / ||f|| of the
+ * averaged interface values (the stop test of Sec. 6).  Sec. 4's stochastic
+ * search over p is served by osm_sample_p, which runs many p values as one
+ * batched Schwarz run.
+ *
+ * Conventions shared by every entry point
+ *  - Host pointers ("host") are read during the call only; the caller keeps
+ *    ownership.  Device pointers ("device") must be cudaMalloc'ed memory on
+ *    the device that was current at osm_setup; the caller owns them too.
+ *  - All device work is enqueued on the CUDA stream given to osm_setup.
+ *    Entry points that return results on the host synchronise that stream.
+ *  - Element-indexed arrays are x-fastest: e = ex + nx (ey + ny ez).
+ *    Node-indexed arrays cover the full (2nx+1)(2ny+1)(2nz+1) Q2 node grid,
+ *    x-fastest, Dirichlet nodes included (their value is 0).
+ *  - Subdomain s = a + sx (b + sy c) owns elements [cx[a], cx[a+1]) x
+ *    [cy[b], cy[b+1]) x [cz[c], cz[c+1]).  Its unknowns are the nodes of its
+ *    closed element box that are not on the outer boundary; interface nodes
+ *    are duplicated in every subdomain that touches them.
+ *  - "Canonical local layout": the unknowns of subdomain 0, then 1, ...,
+ *    each subdomain's unknowns in ascending node index.
+ *  - "Canonical face layout": interface faces ordered x-normal faces first
+ *    (loops c, b, a with a fastest), then y-normal, then z-normal; face f
+ *    between s < t holds 2 n_f values: the datum received by s from t for its
+ *    n_f non-Dirichlet nodes in ascending node index, then the datum received
+ *    by t from s in the same node order.
+ *  - Every function returns an osm_status; on failure the handle's
+ *    osm_last_error() text says why.  No entry point aborts the process.
+ */
+#ifndef OSM_H
+#define OSM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct osm_ctx *osm_handle;   /* opaque, owned by the library */
+
+typedef enum {
+    OSM_OK = 0,
+    OSM_E_ARG = 1,        /* invalid argument (sizes, p <= 0, null pointer) */
+    OSM_E_CUDA = 2,       /* a CUDA runtime call failed */
+    OSM_E_NOMEM = 3,      /* device or host allocation failed */
+    OSM_E_NOCONV = 4,     /* iteration cap reached; outputs are still written */
+    OSM_E_BREAKDOWN = 5,  /* CG breakdown (p.Ap <= 0 or non-finite) */
+    OSM_E_STATE = 6,      /* call not valid in the handle's current state */
+    OSM_E_TIMEOUT = 7     /* a bounded device wait gave up */
+} osm_status;
+
+typedef enum {
+    OSM_FP64 = 0,   /* every step in FP64 */
+    OSM_MIXED = 1   /* FP32 subdomain CG inside FP64 refinement (see osm_opts) */
+} osm_precision;
+
+typedef struct {
+    int32_t nx, ny, nz;            /* elements per direction, >= 1 */
+    const double *xc, *yc, *zc;    /* host; nx+1, ny+1, nz+1 strictly increasing
+                                      vertex coordinates (axis-aligned tensor mesh,
+                                      so graded meshes are allowed) */
+} osm_mesh;
+
+typedef struct {
+    int32_t sx, sy, sz;            /* subdomains per direction, >= 1 */
+    const int32_t *cx, *cy, *cz;   /* host; s+1 element-index cuts, 0 = c[0] < ... < c[s] = n */
+} osm_decomp;
+
+typedef struct {
+    osm_precision prec;
+    double inner_rtol;      /* FP64 subdomain CG stop ||b_i - A_i u_i|| <= inner_rtol ||b_i||
+                               (Sec. 6 uses 1e-10) */
+    double mixed_inner_rtol;/* OSM_MIXED: FP32 CG stop on each correction, relative to the
+                               FP64 defect (default 1e-5) */
+    int32_t max_outer;      /* Schwarz iteration cap (default 10000) */
+    int32_t max_inner;      /* CG iteration cap per subdomain solve (default 20000) */
+    int32_t use_graph;      /* 1 (default): the whole solve runs as one CUDA graph with
+                               device-side while loops; 0: host-driven loop (debugging) */
+    int32_t max_seconds;    /* device wall-clock limit of one solve (default 900): past it
+                               both loops stop and the call returns OSM_E_TIMEOUT */
+    int32_t reserved[4];
+} osm_opts;
+
+typedef struct {
+    int32_t n_sub, n_face;
+    int64_t n_nodes;        /* full node grid */
+    int64_t n_dofs;         /* global unknowns (interior nodes) */
+    int64_t n_local;        /* sum of subdomain unknowns (canonical local layout length) */
+    int64_t n_face_vals;    /* canonical face layout length (2 * sum n_f) */
+    int64_t nnz;            /* sum of subdomain matrix nonzeros (algorithmic) */
+    int64_t sell_entries;   /* stored SELL entries (nonzeros + padding) */
+    int64_t n_slices;       /* SELL slices of 32 rows */
+    int64_t vec_rows;       /* padded device vector length */
+    int64_t device_bytes;   /* device memory held by the handle */
+    double setup_seconds;   /* host assembly + upload wall time */
+} osm_info_t;
+
+typedef struct {
+    int32_t n_outer;        /* Schwarz iterations of the last solve / iterate call */
+    int32_t n_cg_steps;     /* batched CG iterations summed over those Schwarz iterations */
+    int64_t n_launches;     /* kernels the call launched on the GPU */
+    double relres;          /* last stop-test value */
+    int32_t status;         /* bit 0: a subdomain CG hit max_inner; bit 1: CG breakdown */
+    int32_t reserved;
+} osm_stats_t;
+
+/* Fill *o with the defaults listed in osm_opts. */
+void osm_default_opts(osm_opts *o);
+
+/*
+ * Assemble every subdomain system on the host from the closed-form Q2
+ * tensor-product element matrices, pack it for the GPU and upload it.
+ * drho: host, nx*ny*nz per-element constant density anomalies (kg/m^3);
+ * the load is 4 pi G drho with G = 6.672e-11 (Sec. 2).  opts may be NULL
+ * (defaults).  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * The Robin parameter starts at p = 1 for every subdomain; call osm_set_robin.
+ * Errors: OSM_E_ARG for bad sizes or non-increasing coordinates/cuts,
+ * OSM_E_NOMEM / OSM_E_CUDA on allocation or upload failure.  When a handle
+ * was created before the failure, *out is still set so that
+ * osm_last_error() can be read; the caller then calls osm_destroy on it.
+ */
+osm_status osm_setup(const osm_mesh *mesh, const double *drho, const osm_decomp *dec,
+                     const osm_opts *opts, void *cuda_stream, osm_handle *out);
+
+/* Sizes and memory of a handle. */
+osm_status osm_info(osm_handle h, osm_info_t *out);
+
+/* Replace the density (host array, nx*ny*nz); rebuilds the load only. */
+osm_status osm_set_density(osm_handle h, const double *drho);
+
+/* Robin parameter p > 0 on every subdomain (Sec. 3, A = p).  OSM_E_ARG if
+ * p <= 0 or not finite. */
+osm_status osm_set_robin(osm_handle h, double p);
+
+/* One Robin parameter per subdomain (host, n_sub values, all > 0): the
+ * unsymmetric form where subdomain i uses p_i and the exchange uses p_i + p_j. */
+osm_status osm_set_robin_sub(osm_handle h, const double *p_sub);
+
+/*
+ * Full Schwarz solve from u = 0, lam = 0 until ||f - K ubar|| <= rtol ||f||.
+ * phi: device, n_nodes doubles (may be NULL): the averaged solution ubar on
+ * the full node grid.  iters / relres: host (may be NULL): Schwarz iterations
+ * done and the final relative residual.  Returns OSM_E_NOCONV when max_outer
+ * is reached (outputs written) and OSM_E_BREAKDOWN on a CG breakdown.
+ */
+osm_status osm_solve(osm_handle h, double rtol, double *phi, int32_t *iters, double *relres);
+
+/*
+ * Batched stochastic evaluation of Robin parameters (Sec. 4): n_p candidate
+ * values p_host[k] > 0 (host) are run as one batched Schwarz solve sharing
+ * the subdomain stiffness matrices, each from u = 0 with its own state and
+ * convergence mask, to rtol or max_outer iterations.  iters_host /
+ * relres_host (host, n_p each) receive the Schwarz iteration count and final
+ * relative residual per candidate; best_idx (host) the fastest-converging
+ * candidate (fewest iterations among those that reached rtol, ties to the
+ * lower residual, then the smaller p; -1 if none converged).
+ */
+osm_status osm_sample_p(osm_handle h, int32_t n_p, const double *p_host, double rtol,
+                        int32_t max_outer, int32_t *iters_host, double *relres_host,
+                        int32_t *best_idx);
+
+/* SplitMix64 (Steele, Lea & Flood 2014) log-uniform samples in [lo, hi]:
+ * p = exp(log lo + u (log hi - log lo)), u = (x >> 11) * 2^-53, x the k-th
+ * output after seeding the state with `seed`.  p_host: host, n values. */
+osm_status osm_log_uniform_p(uint64_t seed, int32_t n, double lo, double hi, double *p_host);
+
+/* ----------------------------------------------------------------------
+ * Step-level entry points (used by the parity tests; same conventions).
+ * ---------------------------------------------------------------------- */
+
+/* y = A x per subdomain with x, y in the canonical local layout (device,
+ * n_local doubles each).  op 0: A_i = K_i + p_i M_Gi (the Robin matrix);
+ * op 1: A_i = K_i (Neumann stiffness). */
+osm_status osm_apply(osm_handle h, int32_t op, const double *x, double *y);
+
+/* Zero the subdomain iterates u_i and the Robin data lam. */
+osm_status osm_reset(osm_handle h);
+
+/* n Schwarz iterations continuing from the current state, no stop test
+ * other than the caps.  relres_hist: host, n doubles (may be NULL), the
+ * stop-test residual after each iteration. */
+osm_status osm_iterate(osm_handle h, int32_t n, double *relres_hist);
+
+/* Copy the subdomain iterates u_i out in the canonical local layout (device). */
+osm_status osm_get_local(osm_handle h, double *u);
+
+/* Copy the Robin data out / in, canonical face layout (device). */
+osm_status osm_get_lambda(osm_handle h, double *lam);
+osm_status osm_set_lambda(osm_handle h, const double *lam);
+
+/* Counters of the last osm_solve / osm_iterate call (host). */
+osm_status osm_stats(osm_handle h, osm_stats_t *out);
+
+/* CG iteration counts of the last subdomain solves (host, n_sub values). */
+osm_status osm_inner_iters(osm_handle h, int32_t *iters);
+
+/*
+ * Host-only checks of the packing (no GPU needed).  Both assemble and pack
+ * the problem exactly as osm_setup does and then unpack one piece of it.
+ *
+ * osm_host_local_system: subdomain `sub`'s Robin matrix A_i = K_i + p M_Gi
+ * (unpacked from the SELL arrays) and load f_i, in its canonical local
+ * numbering, as CSR with ascending columns.  Call once with rowptr == NULL
+ * to get *n and *nnz, then with rowptr[n+1], col[nnz], val[nnz], f[n] (host).
+ *
+ * osm_host_face_system: interface face `face` (canonical face order): the
+ * node index of each of its n_f nodes and its face mass M_Gst as CSR over
+ * the face nodes.  Same two-call protocol: node[n], rowptr[n+1], col[nnz],
+ * val[nnz] (host).
+ */
+osm_status osm_host_local_system(const osm_mesh *mesh, const double *drho, const osm_decomp *dec,
+                                 double p, int32_t sub, int64_t *n, int64_t *nnz, int64_t *rowptr,
+                                 int32_t *col, double *val, double *f);
+osm_status osm_host_face_system(const osm_mesh *mesh, const double *drho, const osm_decomp *dec,
+                                int32_t face, int64_t *n, int64_t *nnz, int32_t *node,
+                                int64_t *rowptr, int32_t *col, double *val);
+
+/* Time the batched SELL SpMV kernel alone: `reps` back-to-back launches of
+ * y = A x over every subdomain (the operator of the CG step) between two CUDA
+ * events on the handle's stream, after one untimed launch.  *ms receives the
+ * mean time per launch in milliseconds (host).  The solver state is not
+ * changed. */
+osm_status osm_profile_spmv(osm_handle h, int32_t reps, double *ms);
+
+/* Static description of a status code. */
+const char *osm_status_string(osm_status s);
+
+/* Text of the last error on this handle ("" if none); valid until the next call. */
+const char *osm_last_error(osm_handle h);
+
+/* Free every device and host resource of the handle (NULL is ignored). */
+void osm_destroy(osm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSM_H */

@@ -1,0 +1,340 @@
+"""ctypes binding of libosm.so (include/osm.h).  Argument marshalling only:
+every step of the solve runs in the library's CUDA kernels.  PyTorch is used
+for device memory and the current CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libosm.so")
+
+OSM_OK, OSM_E_ARG, OSM_E_CUDA, OSM_E_NOMEM, OSM_E_NOCONV, OSM_E_BREAKDOWN, OSM_E_STATE, OSM_E_TIMEOUT = range(8)
+OSM_FP64, OSM_MIXED = 0, 1
+
+EXPORTED = (
+    "osm_default_opts", "osm_setup", "osm_info", "osm_set_density", "osm_set_robin",
+    "osm_set_robin_sub", "osm_solve", "osm_sample_p", "osm_log_uniform_p", "osm_apply",
+    "osm_reset", "osm_iterate", "osm_get_local", "osm_get_lambda", "osm_set_lambda",
+    "osm_inner_iters", "osm_stats", "osm_host_local_system", "osm_host_face_system", "osm_profile_spmv",
+    "osm_status_string",
+    "osm_last_error", "osm_destroy",
+)
+
+
+class OsmMesh(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("xc", C.c_void_p), ("yc", C.c_void_p), ("zc", C.c_void_p)]
+
+
+class OsmDecomp(C.Structure):
+    _fields_ = [("sx", C.c_int32), ("sy", C.c_int32), ("sz", C.c_int32),
+                ("cx", C.c_void_p), ("cy", C.c_void_p), ("cz", C.c_void_p)]
+
+
+class OsmOpts(C.Structure):
+    _fields_ = [("prec", C.c_int32), ("inner_rtol", C.c_double), ("mixed_inner_rtol", C.c_double),
+                ("max_outer", C.c_int32), ("max_inner", C.c_int32), ("use_graph", C.c_int32),
+                ("max_seconds", C.c_int32), ("reserved", C.c_int32 * 4)]
+
+
+class OsmInfo(C.Structure):
+    _fields_ = [("n_sub", C.c_int32), ("n_face", C.c_int32), ("n_nodes", C.c_int64),
+                ("n_dofs", C.c_int64), ("n_local", C.c_int64), ("n_face_vals", C.c_int64),
+                ("nnz", C.c_int64), ("sell_entries", C.c_int64), ("n_slices", C.c_int64),
+                ("vec_rows", C.c_int64),
+                ("device_bytes", C.c_int64), ("setup_seconds", C.c_double)]
+
+
+class OsmStats(C.Structure):
+    _fields_ = [("n_outer", C.c_int32), ("n_cg_steps", C.c_int32), ("n_launches", C.c_int64),
+                ("relres", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32)]
+
+
+class OsmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libosm.so; fails loudly if the CUDA library has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libosm.so is missing ({LIB_PATH}); build it with "
+                          "paper_2112_03851_gb300.build.build()")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "osm_default_opts": (None, [vp]),
+        "osm_setup": (C.c_int, [vp, vp, vp, vp, vp, vp]),
+        "osm_info": (C.c_int, [vp, vp]),
+        "osm_set_density": (C.c_int, [vp, vp]),
+        "osm_set_robin": (C.c_int, [vp, d]),
+        "osm_set_robin_sub": (C.c_int, [vp, vp]),
+        "osm_solve": (C.c_int, [vp, d, vp, vp, vp]),
+        "osm_sample_p": (C.c_int, [vp, i32, vp, d, i32, vp, vp, vp]),
+        "osm_log_uniform_p": (C.c_int, [C.c_uint64, i32, d, d, vp]),
+        "osm_apply": (C.c_int, [vp, i32, vp, vp]),
+        "osm_reset": (C.c_int, [vp]),
+        "osm_iterate": (C.c_int, [vp, i32, vp]),
+        "osm_get_local": (C.c_int, [vp, vp]),
+        "osm_get_lambda": (C.c_int, [vp, vp]),
+        "osm_set_lambda": (C.c_int, [vp, vp]),
+        "osm_inner_iters": (C.c_int, [vp, vp]),
+        "osm_stats": (C.c_int, [vp, vp]),
+        "osm_host_local_system": (C.c_int, [vp, vp, vp, d, i32, vp, vp, vp, vp, vp, vp]),
+        "osm_host_face_system": (C.c_int, [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]),
+        "osm_profile_spmv": (C.c_int, [vp, i32, vp]),
+        "osm_status_string": (C.c_char_p, [C.c_int]),
+        "osm_last_error": (C.c_char_p, [vp]),
+        "osm_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _status_name(st):
+    try:
+        return load().osm_status_string(st).decode()
+    except Exception:
+        return f"status {st}"
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _dptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+class _Inputs:
+    """Host copies of mesh / density / cuts kept alive for a call."""
+
+    def __init__(self, xc, yc, zc, drho, cx, cy, cz):
+        self.xc = np.ascontiguousarray(xc, dtype=np.float64)
+        self.yc = np.ascontiguousarray(yc, dtype=np.float64)
+        self.zc = np.ascontiguousarray(zc, dtype=np.float64)
+        self.drho = np.ascontiguousarray(drho, dtype=np.float64).reshape(-1)
+        self.cx = np.ascontiguousarray(cx, dtype=np.int32)
+        self.cy = np.ascontiguousarray(cy, dtype=np.int32)
+        self.cz = np.ascontiguousarray(cz, dtype=np.int32)
+        nx, ny, nz = len(self.xc) - 1, len(self.yc) - 1, len(self.zc) - 1
+        if self.drho.size != nx * ny * nz:
+            raise ValueError("density must have nx*ny*nz entries")
+        self.mesh = OsmMesh(nx, ny, nz, _ptr(self.xc).value, _ptr(self.yc).value, _ptr(self.zc).value)
+        self.dec = OsmDecomp(len(self.cx) - 1, len(self.cy) - 1, len(self.cz) - 1,
+                             _ptr(self.cx).value, _ptr(self.cy).value, _ptr(self.cz).value)
+
+
+def default_opts(**kw) -> OsmOpts:
+    o = OsmOpts()
+    load().osm_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "prec" and isinstance(v, str):
+            v = {"fp64": OSM_FP64, "mixed": OSM_MIXED}[v]
+        setattr(o, k, v)
+    return o
+
+
+class Solver:
+    """One gravimetry problem on the GPU (a libosm handle).
+
+    ``xc, yc, zc``: element vertex coordinates; ``drho``: per-element density
+    (x fastest); ``cx, cy, cz``: element-index cuts of the subdomain grid.
+    """
+
+    def __init__(self, xc, yc, zc, drho, cx, cy, cz, p=1.0, stream=None, **opts):
+        import torch
+        L = load()
+        self._torch = torch
+        self._in = _Inputs(xc, yc, zc, drho, cx, cy, cz)
+        self.opts = default_opts(**opts)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h = C.c_void_p()
+        st = L.osm_setup(C.byref(self._in.mesh), _ptr(self._in.drho), C.byref(self._in.dec),
+                         C.byref(self.opts), C.c_void_p(stream.cuda_stream), C.byref(h))
+        self._h = h
+        if st != OSM_OK:
+            msg = L.osm_last_error(h).decode() if h.value else ""
+            self.close()
+            raise OsmError(st, msg)
+        info = OsmInfo()
+        L.osm_info(h, C.byref(info))
+        self.info = {k: getattr(info, k) for k, _ in OsmInfo._fields_}
+        if p is not None:
+            if np.ndim(p) == 0:
+                self.set_robin(float(p))
+            else:
+                self.set_robin_sub(p)
+
+    @classmethod
+    def from_problem(cls, prob, p=None, **opts):
+        return cls(prob.xc, prob.yc, prob.zc, prob.drho, prob.cx, prob.cy, prob.cz,
+                   p=prob.p if p is None else p, **opts)
+
+    # ------------------------------------------------------------ plumbing
+    def _check(self, st, allow=()):
+        if st != OSM_OK and st not in allow:
+            raise OsmError(st, load().osm_last_error(self._h).decode())
+        return st
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            load().osm_destroy(h)
+        self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _zeros(self, n, dtype=None):
+        t = self._torch
+        return t.zeros(int(n), dtype=dtype or t.float64, device=self.device)
+
+    # ----------------------------------------------------------------- API
+    def set_robin(self, p: float):
+        self._check(load().osm_set_robin(self._h, float(p)))
+
+    def set_robin_sub(self, p_sub):
+        p_sub = np.ascontiguousarray(p_sub, dtype=np.float64)
+        self._check(load().osm_set_robin_sub(self._h, _ptr(p_sub)))
+
+    def set_density(self, drho):
+        drho = np.ascontiguousarray(drho, dtype=np.float64).reshape(-1)
+        self._check(load().osm_set_density(self._h, _ptr(drho)))
+
+    def solve(self, rtol=1e-8, phi=None, allow_noconv=False):
+        """Full Schwarz solve; returns (phi on the node grid, iterations, relres)."""
+        if phi is None:
+            phi = self._zeros(self.info["n_nodes"])
+        it = C.c_int32()
+        rel = C.c_double()
+        allow = (OSM_E_NOCONV,) if allow_noconv else ()
+        self._check(load().osm_solve(self._h, float(rtol), _dptr(phi), C.byref(it), C.byref(rel)), allow)
+        return phi, it.value, rel.value
+
+    def apply(self, x, op=0):
+        """y = A x (op 0: Robin matrix, op 1: Neumann stiffness), canonical local layout."""
+        x = x.contiguous()
+        y = self._zeros(self.info["n_local"])
+        self._check(load().osm_apply(self._h, int(op), _dptr(x), _dptr(y)))
+        return y
+
+    def reset(self):
+        self._check(load().osm_reset(self._h))
+
+    def iterate(self, n):
+        hist = np.zeros(max(int(n), 1))
+        self._check(load().osm_iterate(self._h, int(n), _ptr(hist)))
+        return hist[:n]
+
+    def get_local(self):
+        u = self._zeros(self.info["n_local"])
+        self._check(load().osm_get_local(self._h, _dptr(u)))
+        return u
+
+    def get_lambda(self):
+        lam = self._zeros(self.info["n_face_vals"])
+        self._check(load().osm_get_lambda(self._h, _dptr(lam)))
+        return lam
+
+    def set_lambda(self, lam):
+        lam = lam.contiguous()
+        self._check(load().osm_set_lambda(self._h, _dptr(lam)))
+
+    def stats(self):
+        st = OsmStats()
+        self._check(load().osm_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in OsmStats._fields_ if k != "reserved"}
+
+    def inner_iters(self):
+        it = np.zeros(self.info["n_sub"], dtype=np.int32)
+        self._check(load().osm_inner_iters(self._h, _ptr(it)))
+        return it
+
+    def profile_spmv(self, reps=20):
+        """Mean time (ms) of one batched SELL SpMV launch, CUDA events."""
+        ms = C.c_double()
+        self._check(load().osm_profile_spmv(self._h, int(reps), C.byref(ms)))
+        return ms.value
+
+    def spmv_bytes(self):
+        """Algorithmic bytes of one SpMV: nnz (8 B value + 4 B column), 8 B per
+        slice offset, the input vector read once and the output written once."""
+        i = self.info
+        return i["nnz"] * 12 + i["n_slices"] * 8 + i["n_local"] * 16
+
+    def sample_p(self, p_values, rtol=1e-8, max_outer=None):
+        p = np.ascontiguousarray(p_values, dtype=np.float64)
+        n = len(p)
+        iters = np.zeros(n, dtype=np.int32)
+        rel = np.zeros(n)
+        best = C.c_int32(-1)
+        mo = self.opts.max_outer if max_outer is None else int(max_outer)
+        self._check(load().osm_sample_p(self._h, n, _ptr(p), float(rtol), mo, _ptr(iters), _ptr(rel),
+                                        C.byref(best)), (OSM_E_NOCONV,))
+        return iters, rel, best.value
+
+
+def log_uniform_p(seed: int, n: int, lo: float, hi: float) -> np.ndarray:
+    out = np.zeros(n)
+    st = load().osm_log_uniform_p(C.c_uint64(seed), int(n), float(lo), float(hi), _ptr(out))
+    if st != OSM_OK:
+        raise OsmError(st, "bad arguments")
+    return out
+
+
+def host_local_system(xc, yc, zc, drho, cx, cy, cz, p, sub):
+    """(A_i as scipy CSR, f_i) unpacked from the GPU packing (host only)."""
+    import scipy.sparse as sp
+    L = load()
+    inp = _Inputs(xc, yc, zc, drho, cx, cy, cz)
+    n, nnz = C.c_int64(), C.c_int64()
+    args = (C.byref(inp.mesh), _ptr(inp.drho), C.byref(inp.dec), float(p), int(sub))
+    st = L.osm_host_local_system(*args, C.byref(n), C.byref(nnz), None, None, None, None)
+    if st != OSM_OK:
+        raise OsmError(st, "host_local_system")
+    rp = np.zeros(n.value + 1, dtype=np.int64)
+    ci = np.zeros(nnz.value, dtype=np.int32)
+    v = np.zeros(nnz.value)
+    f = np.zeros(n.value)
+    L.osm_host_local_system(*args, C.byref(n), C.byref(nnz), _ptr(rp), _ptr(ci), _ptr(v), _ptr(f))
+    return sp.csr_matrix((v, ci, rp), shape=(n.value, n.value)), f
+
+
+def host_face_system(xc, yc, zc, drho, cx, cy, cz, face):
+    """(node indices, face mass as scipy CSR) of one face (host only)."""
+    import scipy.sparse as sp
+    L = load()
+    inp = _Inputs(xc, yc, zc, drho, cx, cy, cz)
+    n, nnz = C.c_int64(), C.c_int64()
+    args = (C.byref(inp.mesh), _ptr(inp.drho), C.byref(inp.dec), int(face))
+    st = L.osm_host_face_system(*args, C.byref(n), C.byref(nnz), None, None, None, None)
+    if st != OSM_OK:
+        raise OsmError(st, "host_face_system")
+    node = np.zeros(n.value, dtype=np.int32)
+    rp = np.zeros(n.value + 1, dtype=np.int64)
+    ci = np.zeros(nnz.value, dtype=np.int32)
+    v = np.zeros(nnz.value)
+    L.osm_host_face_system(*args, C.byref(n), C.byref(nnz), _ptr(node), _ptr(rp), _ptr(ci), _ptr(v))
+    return node, sp.csr_matrix((v, ci, rp), shape=(n.value, n.value))

@@ -1,0 +1,194 @@
+// Internal declarations of libosm: host-side problem description, device
+// buffers and kernel launchers.  Not part of the public ABI (include/osm.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/osm.h"
+
+namespace osm {
+
+// Rows of one SELL slice (one warp, one lane per row) and rows per CTA tile.
+constexpr int kSliceRows = 32;
+constexpr int kTileRows = 256;
+constexpr int kTileSlices = kTileRows / kSliceRows;
+// SELL row widths are padded to a multiple of 4 so that every lane can load
+// four column indices (int4) and two value pairs (double2) per step.
+constexpr int kWidthQuantum = 4;
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kGravity = 6.672e-11;  // Sec. 2
+
+// ---------------------------------------------------------------- host side
+
+// One subdomain's element box and its place in the device arrays.
+struct SubInfo {
+  int ex0, ex1, ey0, ey1, ez0, ez1;   // element ranges
+  int i0, i1, j0, j1, k0, k1;         // node box (inclusive)
+  int32_t n;                          // unknowns
+  int32_t npad;                       // rows padded to kTileRows
+  int64_t voff;                       // first vector row
+  int64_t canon_off;                  // first canonical-layout index
+  int64_t tile0;                      // first tile
+  int64_t slice0;                     // first slice
+  bool iface[6];                      // -x, +x, -y, +y, -z, +z side is an interface
+};
+
+// Everything the host builds before upload.
+struct HostProblem {
+  int nx, ny, nz, NX, NY, NZ;
+  int sx, sy, sz, nsub;
+  std::vector<double> xc, yc, zc;
+  std::vector<SubInfo> sub;
+  int64_t n_nodes = 0, n_dofs = 0, n_local = 0, vec_rows = 0, n_tiles = 0, n_slices = 0;
+  int64_t nnz = 0, sell_entries = 0;
+
+  // SELL-32 storage of K_i (p = 0); slice s holds 32 rows x width w entries
+  // at [slice_off[s], slice_off[s+1]), laid out so that lane l of step q
+  // reads cols[off + 128 q + 4 l .. +3] and vals[off + 128 q + 4 l .. +3] as
+  // two double2 at off + 64 (2q) + 2 l and off + 64 (2q+1) + 2 l.
+  std::vector<int64_t> slice_off;
+  std::vector<int32_t> cols;          // subdomain-local row index (internal order)
+  std::vector<double> vals;
+
+  std::vector<int32_t> tile_sub;      // tile -> subdomain
+  std::vector<int32_t> row_sub;       // not stored on device; per vector row
+  std::vector<int32_t> can2vec;       // canonical local index -> vector row
+  std::vector<double> f;              // load per vector row
+  std::vector<double> kdiag;          // diag(K_i) per vector row
+  std::vector<double> dinv0;          // 1 / diag(K_i) (padding rows: 0)
+
+  // Interface rows: rows of subdomain i lying on a face with a neighbour.
+  std::vector<int32_t> irow;          // vector row
+  std::vector<int32_t> irow_sub;      // its subdomain
+  std::vector<double> irow_mdiag;     // diag(M_Gi) on that row
+  std::vector<int32_t> ilam_ptr;      // -> lam indices of data received at this row
+  std::vector<int32_t> ilam;
+  std::vector<int32_t> im_ptr;        // -> entries of M_Gi in this row
+  std::vector<int32_t> im_col;        // vector row of the column
+  std::vector<double> im_val;         // M_Gi value
+  std::vector<int64_t> im_pos;        // position of the entry in the SELL value array
+  std::vector<double> im_kval;        // K_i value at that position
+
+  // Faces (canonical face layout) and their mass matrices.
+  int nface = 0;
+  std::vector<int32_t> face_s, face_t, face_n;
+  std::vector<int64_t> face_eo;       // first face entry (lam offset is 2*eo)
+  int64_t n_fent = 0;
+  std::vector<int32_t> fent_face;     // entry -> face
+  std::vector<int32_t> fent_row_s, fent_row_t;  // vector rows on the two sides
+  std::vector<int32_t> fm_ptr;        // face mass CSR over entries
+  std::vector<int32_t> fm_col;        // global entry index
+  std::vector<double> fm_val;
+
+  // Copies of each node of the full grid (vector rows, subdomain order).
+  std::vector<int32_t> cp_ptr;        // n_nodes + 1
+  std::vector<int32_t> cp_idx;
+};
+
+// Build everything on the host.  Returns an empty string on success, else
+// the reason of the failure.
+std::string build_host_problem(const osm_mesh& mesh, const double* drho, const osm_decomp& dec,
+                               HostProblem& hp);
+
+// Rebuild the load vector (per vector row) for a new density.
+void build_load(const HostProblem& hp, const double* drho, std::vector<double>& f);
+
+// ------------------------------------------------------------- device side
+
+// Per-subdomain CG scalars and status (device arrays of n_sub entries).
+struct DevSubState {
+  double* rho;      // r.z
+  double* alpha;
+  double* beta;
+  double* bb;       // ||b||^2
+  double* rr;       // ||r||^2
+  int32_t* active;  // 1 while the subdomain's CG runs
+  int32_t* iters;   // CG iterations of the current solve
+  int32_t* status;  // 0 ok, 1 cap reached, 2 breakdown
+  unsigned* cnt_a;  // last-block counters, one set per kernel
+  unsigned* cnt_b;
+  unsigned* cnt_i;
+};
+
+// Loop-control block living in device memory.
+struct DevCtl {
+  double rtol;            // Schwarz stop
+  double tau2;            // inner_rtol^2
+  int32_t max_outer;
+  int32_t max_inner;
+  int32_t n_outer;        // Schwarz iterations done
+  int32_t n_inner;        // CG iterations of the current subdomain solve
+  int32_t n_active;       // subdomains still iterating
+  int32_t status;         // OR of subdomain statuses seen in this solve
+  int32_t total_inner;    // batched CG steps summed over the Schwarz iterations
+  int32_t pad0;
+  double relres;          // last stop-test value
+  unsigned long long t_start_ns;  // %globaltimer at the first kernel of the call
+  unsigned long long t_limit_ns;  // wall-clock budget of the call
+  int32_t stop;           // set once the budget is exhausted: both loops end
+  int32_t pad1;
+  unsigned gcnt_b;        // global last-block counters
+  unsigned gcnt_i;
+  unsigned gcnt_r;
+  unsigned pad;
+};
+
+struct DevProblem {
+  // SELL
+  const int64_t* slice_off;
+  const int32_t* cols;
+  double* vals;
+  const int32_t* tile_sub;
+  const int64_t* sub_tile0;   // n_sub + 1
+  int64_t n_tiles;
+  // vectors (vec_rows each)
+  double *x, *r, *z, *p, *q, *b, *f, *dinv, *w, *y;
+  // per subdomain
+  double* psub;
+  DevSubState st;
+  // per tile partials
+  double *part0, *part1, *part2;
+  // interface rows
+  int32_t n_irow;
+  const int32_t *irow, *irow_sub, *ilam_ptr, *ilam, *im_ptr, *im_col;
+  const double *irow_mdiag, *im_val, *im_kval;
+  const int64_t* im_pos;
+  const double* kdiag;
+  // faces
+  int64_t n_fent;
+  const int32_t *fent_face, *fent_row_s, *fent_row_t, *fm_ptr, *fm_col;
+  const double* fm_val;
+  const int32_t *face_s, *face_t, *face_n;
+  const int64_t* face_eo;
+  double* lam;
+  // copies
+  int64_t n_nodes;
+  const int32_t *cp_ptr, *cp_idx;
+  double* phi;          // internal full-grid output
+  double* rpart;        // residual partials (per block)
+  double* rpart2;
+  int64_t n_rblocks;
+  double* hist;         // residual history (max_outer)
+  DevCtl* ctl;
+  const int32_t* can2vec;
+  int64_t n_local;
+};
+
+// Kernel launchers (osm_kernels.cu).  All enqueue on `s` and return the
+// launch error.  `cond` / `use_cond` name the graph conditional to drive.
+cudaError_t launch_set_robin(const DevProblem& d, cudaStream_t s);
+cudaError_t launch_rhs_gather(const DevProblem& d, cudaStream_t s);
+cudaError_t launch_cg_init(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
+cudaError_t launch_cg_iteration(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
+cudaError_t launch_exchange(const DevProblem& d, cudaStream_t s);
+cudaError_t launch_residual(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
+cudaError_t launch_apply(const DevProblem& d, int op, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_gather_local(const DevProblem& d, const double* vec, double* canon, cudaStream_t s);
+cudaError_t launch_spmv_plain(const DevProblem& d, const double* x, double* y, cudaStream_t s);
+
+}  // namespace osm

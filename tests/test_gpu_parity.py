@@ -1,0 +1,213 @@
+"""GPU parity of the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (FP64 everywhere):
+* SpMV: |y - y_ref| <= 1e-13 (|A| |x|)_row -- a row has at most 125 terms,
+  so the rounding error of either side is below 125 * 2^-53 |A||x| ~ 1.4e-14.
+* One Schwarz iteration: the local CG solves stop at a relative residual of
+  1e-12 on both sides, so iterates agree to ~1e-11 relative.
+* Full solves: the relative L2 distance to the monolithic oracle solution is
+  <= 1e-10 (the target for FP64), and the Schwarz iteration count equals the
+  oracle's sequential Schwarz within +-1.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def osm(cuda_ok):
+    from paper_2112_03851_gb300 import build
+    build.build()
+    import paper_2112_03851_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def small_uneven():
+    return gen.regional_problem(nx=12, ny=10, nz=8, sx=3, sy=2, sz=2, p=2.0, seed=4,
+                                lx=10.0, ly=8.0, lz=3.0)
+
+
+def _oracle_blocks(prob, p):
+    S = oracle.Schwarz(prob.xc, prob.yc, prob.zc, prob.drho, prob.cx, prob.cy, prob.cz, p)
+    blocks = [S.sub_export(s) for s in range(S.nsub)]
+    return S, blocks
+
+
+@pytest.mark.parametrize("case", ["sphere16", "uneven"])
+@pytest.mark.parametrize("op", [0, 1])
+def test_apply_matches_oracle(osm, case, op):
+    torch = _torch()
+    prob = gen.sphere_problem(16, 2, 10.0) if case == "sphere16" else small_uneven()
+    p = 3.3
+    S, blocks = _oracle_blocks(prob, p)
+    sol = osm.Solver.from_problem(prob, p=p)
+    rng = np.random.default_rng(11)
+    x = rng.standard_normal(sol.info["n_local"])
+    y = sol.apply(torch.from_numpy(x).cuda(), op=op).cpu().numpy()
+    off = 0
+    for s, (A, f, g, _) in enumerate(blocks):
+        n = A.shape[0]
+        xs = x[off:off + n]
+        if op == 1:  # Neumann stiffness: remove p M_G again
+            A = A - p * _face_mass_local(S, s, g)
+        ref = A @ xs
+        bound = abs(A) @ np.abs(xs)
+        assert np.all(np.abs(y[off:off + n] - ref) <= 1e-13 * bound + 1e-300), (s, op)
+        off += n
+    assert off == len(x)
+
+
+def _face_mass_local(S, s, g):
+    """M_Gs assembled in subdomain s's canonical numbering from the oracle faces."""
+    import scipy.sparse as sp
+    n = len(g)
+    loc = {int(v): i for i, v in enumerate(g)}
+    rows, cols, vals = [], [], []
+    for f in range(S.nface):
+        a, b, _, _ = S.face_info(f)
+        if s not in (a, b):
+            continue
+        gf, Mf = S.face_export(f)
+        li = np.array([loc[int(v)] for v in gf])
+        C = Mf.tocoo()
+        rows.append(li[C.row]); cols.append(li[C.col]); vals.append(C.data)
+    if not rows:
+        return sp.csr_matrix((n, n))
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_first_iterations_match_oracle(osm, use_graph):
+    """Two Schwarz iterations from zero: subdomain iterates, Robin data and
+    stop-test residuals equal the oracle's sequential Schwarz."""
+    torch = _torch()
+    prob = small_uneven()
+    p = 2.0
+    S = oracle.Schwarz.from_problem(prob, p=p)
+    sol = osm.Solver.from_problem(prob, p=p, inner_rtol=1e-12, use_graph=use_graph)
+    sol.reset()
+    for it in range(2):
+        it_ref = S.iterate(inner_rtol=1e-12)
+        _, rel_ref = S.residual()
+        hist = sol.iterate(1)
+        u = sol.get_local().cpu().numpy()
+        u_ref = np.concatenate([S.sub_export(s)[3] for s in range(S.nsub)])
+        assert np.linalg.norm(u - u_ref) <= 1e-10 * np.linalg.norm(u_ref), it
+        lam = sol.get_lambda().cpu().numpy()
+        lam_ref = np.concatenate([np.concatenate([S.get_lambda(f, 0), S.get_lambda(f, 1)])
+                                  for f in range(S.nface)])
+        assert np.linalg.norm(lam - lam_ref) <= 1e-9 * np.linalg.norm(lam_ref), it
+        assert abs(hist[0] - rel_ref) <= 1e-8 * rel_ref, (hist[0], rel_ref)
+        assert np.all(np.abs(sol.inner_iters() - it_ref) <= 1)
+
+
+def _mono(prob):
+    G = oracle.GlobalSystem(prob.xc, prob.yc, prob.zc, prob.drho)
+    ref, _, _ = G.solve(tol=1e-14)
+    return G, G.to_grid(ref)
+
+
+def test_sphere_solve_matches_oracle(osm):
+    """16^3 Q2, 2x2x2 subdomains, p = 10, inner 1e-12, Schwarz to 1e-10."""
+    prob = gen.sphere_problem(16, 2, 10.0)
+    G, ref = _mono(prob)
+    S = oracle.Schwarz.from_problem(prob)
+    _, n_ref, _, _ = S.solve(inner_rtol=1e-12, rtol=1e-10)
+    sol = osm.Solver.from_problem(prob, inner_rtol=1e-12)
+    phi, n, rel = sol.solve(rtol=1e-10)
+    phi = phi.cpu().numpy()
+    assert rel <= 1e-10 and abs(n - n_ref) <= 1
+    assert np.linalg.norm(phi - ref) <= 1e-10 * np.linalg.norm(ref)
+    assert G.residual(phi) <= 1.01e-10
+    # the Dirichlet nodes are exactly zero
+    P = phi.reshape(33, 33, 33)
+    for face in (P[0], P[-1], P[:, 0], P[:, -1], P[:, :, 0], P[:, :, -1]):
+        assert np.all(face == 0.0)
+
+
+def test_uneven_graded_solve_matches_oracle(osm):
+    prob = small_uneven()
+    G, ref = _mono(prob)
+    S = oracle.Schwarz.from_problem(prob)
+    _, n_ref, _, _ = S.solve(inner_rtol=1e-12, rtol=1e-11, max_outer=3000)
+    sol = osm.Solver.from_problem(prob, inner_rtol=1e-12)
+    phi, n, rel = sol.solve(rtol=1e-11)
+    phi = phi.cpu().numpy()
+    assert rel <= 1e-11 and abs(n - n_ref) <= 1
+    assert np.linalg.norm(phi - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_solve_is_deterministic_and_graph_equals_host_loop(osm):
+    prob = gen.sphere_problem(8, 2, 4.0)
+    a = osm.Solver.from_problem(prob, inner_rtol=1e-10)
+    b = osm.Solver.from_problem(prob, inner_rtol=1e-10, use_graph=0)
+    pa, na, ra = a.solve(rtol=1e-9)
+    pa2, na2, ra2 = a.solve(rtol=1e-9)
+    pb, nb, rb = b.solve(rtol=1e-9)
+    assert na == na2 == nb and ra == ra2 == rb
+    assert bool((pa == pa2).all()) and bool((pa == pb).all())
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1, 1), (3, 3, 3, 1), (2, 3, 4, 2), (5, 2, 3, 1)])
+def test_edge_shapes(osm, shape):
+    """Degenerate meshes: a single element (one unknown), one subdomain (no
+    interface: one iteration), one-element-thick subdomains."""
+    nx, ny, nz, s = shape
+    xc, yc, zc = np.linspace(0, 1, nx + 1), np.linspace(0, 2, ny + 1), np.linspace(0, 1.5, nz + 1)
+    rng = np.random.default_rng(nx * 100 + ny * 10 + nz)
+    drho = rng.normal(0, 100, nx * ny * nz)
+    cx = np.linspace(0, nx, min(s, nx) + 1).astype(np.int32) if s > 1 else np.array([0, nx], np.int32)
+    cy = np.array([0, 1, ny], np.int32) if (s > 1 and ny > 1) else np.array([0, ny], np.int32)
+    cz = np.array([0, nz], np.int32)
+    G = oracle.GlobalSystem(xc, yc, zc, drho)
+    ref, _, _ = G.solve(tol=1e-14)
+    ref = G.to_grid(ref)
+    sol = osm.Solver(xc, yc, zc, drho, cx, cy, cz, p=2.0, inner_rtol=1e-13)
+    phi, n, rel = sol.solve(rtol=1e-12)
+    phi = phi.cpu().numpy()
+    if len(cx) == 2 and len(cy) == 2:
+        assert n == 1
+    assert np.linalg.norm(phi - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+def test_argument_errors(osm):
+    prob = gen.sphere_problem(4, 2, 1.0)
+    sol = osm.Solver.from_problem(prob)
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(osm.OsmError):
+            sol.set_robin(bad)
+    with pytest.raises(osm.OsmError):
+        sol.solve(rtol=0.0)
+    with pytest.raises(osm.OsmError):
+        sol.iterate(10 ** 6)
+
+
+def test_noconv_reports_but_writes(osm):
+    prob = gen.sphere_problem(8, 2, 4.0)
+    sol = osm.Solver.from_problem(prob, max_outer=3)
+    with pytest.raises(osm.OsmError) as ei:
+        sol.solve(rtol=1e-12)
+    assert ei.value.status == 4
+    phi, n, rel = sol.solve(rtol=1e-12, allow_noconv=True)
+    assert n == 3 and rel > 1e-12 and float(phi.abs().max()) > 0
+
+
+def test_layered64_full_size_residual(osm):
+    """The 64^3 layered workload (2.05M unknowns, 4x4x4 subdomains) at full
+    size: the oracle's own assembled K certifies ||f - K phi|| <= rtol ||f||."""
+    prob = gen.workload("layered64")
+    sol = osm.Solver.from_problem(prob, p=10.0)
+    phi, n, rel = sol.solve(rtol=1e-8)
+    assert rel <= 1e-8
+    G = oracle.GlobalSystem(prob.xc, prob.yc, prob.zc, prob.drho)
+    assert G.residual(phi.cpu().numpy()) <= 1.001e-8
