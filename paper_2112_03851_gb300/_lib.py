@@ -19,7 +19,7 @@ EXPORTED = (
     "osm_default_opts", "osm_setup", "osm_info", "osm_set_density", "osm_set_robin",
     "osm_set_robin_sub", "osm_solve", "osm_sample_p", "osm_log_uniform_p", "osm_apply",
     "osm_reset", "osm_iterate", "osm_get_local", "osm_get_lambda", "osm_set_lambda",
-    "osm_inner_iters", "osm_stats", "osm_host_local_system", "osm_host_face_system", "osm_profile_spmv",
+    "osm_apply_noalloc", "osm_inner_iters", "osm_stats", "osm_host_local_system", "osm_host_face_system", "osm_profile_spmv",
     "osm_status_string",
     "osm_last_error", "osm_destroy",
 )
@@ -84,6 +84,7 @@ def load():
         "osm_sample_p": (C.c_int, [vp, i32, vp, d, i32, vp, vp, vp]),
         "osm_log_uniform_p": (C.c_int, [C.c_uint64, i32, d, d, vp]),
         "osm_apply": (C.c_int, [vp, i32, vp, vp]),
+        "osm_apply_noalloc": (C.c_int, [vp, i32, vp, vp]),
         "osm_reset": (C.c_int, [vp]),
         "osm_iterate": (C.c_int, [vp, i32, vp]),
         "osm_get_local": (C.c_int, [vp, vp]),
@@ -238,6 +239,15 @@ class Solver:
         x = x.contiguous()
         y = self._zeros(self.info["n_local"])
         self._check(load().osm_apply(self._h, int(op), _dptr(x), _dptr(y)))
+        return y
+
+    def apply_noalloc(self, x, y=None, op=0):
+        """y = A x like apply(), using only the library's fixed scratch (no
+        device allocation by the library; y may be a preallocated tensor)."""
+        x = x.contiguous()
+        if y is None:
+            y = self._zeros(self.info["n_local"])
+        self._check(load().osm_apply_noalloc(self._h, int(op), _dptr(x), _dptr(y)))
         return y
 
     def reset(self):

@@ -275,6 +275,22 @@ osm_status reset_state(osm_ctx* h) {
 
 }  // namespace
 
+namespace osm {
+
+const DevProblem* handle_problem(osm_handle h, cudaStream_t* stream, int64_t* vec_rows, int* device) {
+  if (!h) return nullptr;
+  if (stream) *stream = h->stream;
+  if (vec_rows) *vec_rows = h->hp.vec_rows;
+  if (device) *device = h->device;
+  return &h->d;
+}
+
+void handle_set_error(osm_handle h, const char* msg) {
+  if (h) h->err = msg;
+}
+
+}  // namespace osm
+
 extern "C" {
 
 void osm_default_opts(osm_opts* o) {

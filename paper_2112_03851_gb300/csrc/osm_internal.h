@@ -190,5 +190,14 @@ cudaError_t launch_residual(const DevProblem& d, cudaStream_t s, unsigned long l
 cudaError_t launch_apply(const DevProblem& d, int op, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_gather_local(const DevProblem& d, const double* vec, double* canon, cudaStream_t s);
 cudaError_t launch_spmv_plain(const DevProblem& d, const double* x, double* y, cudaStream_t s);
+// launch_apply with caller-chosen scratch vectors (vec_rows doubles each;
+// w_scratch must be zero on every padding row).
+cudaError_t launch_apply_scratch(const DevProblem& d, int op, const double* x, double* y, double* w_scratch,
+                                 double* y_scratch, cudaStream_t s);
+
+// Access to a handle's device problem for entry points defined outside
+// osm_api.cu.  Returns nullptr for a null handle.
+const DevProblem* handle_problem(osm_handle h, cudaStream_t* stream, int64_t* vec_rows, int* device);
+void handle_set_error(osm_handle h, const char* msg);
 
 }  // namespace osm

@@ -468,6 +468,15 @@ cudaError_t launch_apply(const DevProblem& d, int op, const double* x, double* y
   return cudaGetLastError();
 }
 
+cudaError_t launch_apply_scratch(const DevProblem& d, int op, const double* x, double* y, double* w_scratch,
+                                 double* y_scratch, cudaStream_t s) {
+  k_scatter_local<<<blocks_for(d.n_local, 256), 256, 0, s>>>(d, x, w_scratch);
+  k_spmv_plain<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, w_scratch, y_scratch);
+  if (op == 1 && d.n_irow) k_face_correct<<<blocks_for(d.n_irow, 256), 256, 0, s>>>(d, w_scratch, y_scratch);
+  k_gather_local<<<blocks_for(d.n_local, 256), 256, 0, s>>>(d, y_scratch, y);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gather_local(const DevProblem& d, const double* vec, double* canon, cudaStream_t s) {
   k_gather_local<<<blocks_for(d.n_local, 256), 256, 0, s>>>(d, vec, canon);
   return cudaGetLastError();
