@@ -33,6 +33,7 @@ WORKLOAD = "layered64"
 P_ROBIN = 20.0
 RTOL = 1e-8
 INNER_RTOL = 1e-10
+MIXED_INNER_RTOL = 0.3
 FALLBACK_HBM = 6800.0
 
 
@@ -61,7 +62,7 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
-def _traffic_per_launch(n_local):
+def _traffic_per_launch(n_local, which):
     """DRAM bytes per SpMV launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
     path = os.path.join(ROOT, "profiles", "spmv_traffic.json")
@@ -70,7 +71,7 @@ def _traffic_per_launch(n_local):
             d = json.load(f)
         if d.get("kernel_hash") != _kernel_hash():
             return None
-        return float(d["bytes_per_row"]) * n_local
+        return round(float(d[which]["dram_bytes_per_row"]) * n_local)
     except Exception:
         return None
 
@@ -205,8 +206,74 @@ def _reference_iterations():
         return 150
 
 
-def run_ours(args):
+def _measure(sol, prob, args, ws, local, barrier, use_graph_note):
+    """Warm-up, the timed region (CUDA events, clocks sampled) and the
+    end-to-end run through the public API from host buffers."""
     import numpy as np
+    import torch
+    stream = torch.cuda.current_stream()
+    phi = torch.zeros(sol.info["n_nodes"], dtype=torch.float64, device="cuda")
+    for _ in range(max(args.warmup, 1)):
+        sol.solve(RTOL, phi=phi)
+    st = sol.stats()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    rel = None
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            _, it, rel = sol.solve(RTOL, phi=phi)
+            launches += sol.stats()["n_launches"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    # end to end: new density from a host array in, solution out to pinned
+    # host memory, every step
+    phi_host = torch.empty(sol.info["n_nodes"], dtype=torch.float64, pin_memory=True)
+    drho = np.ascontiguousarray(prob.drho)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        sol.set_density(drho)
+        sol.solve(RTOL, phi=phi)
+        phi_host.copy_(phi, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+    return {
+        "value": ws * prob.n_dofs / (ms_max / 1e3), "ms_per_step": ms_max, "relres": rel,
+        "schwarz_iterations": st["n_outer"], "cg_steps_per_solve": st["n_cg_steps"],
+        "launches_per_step": int(st["n_launches"]), "gpu_launches": int(launches),
+        "clocks": clk.summary(), "launch_mode": use_graph_note,
+        "e2e": {"value": ws * prob.n_dofs / float(te.item()), "unit": "DOF/s",
+                "h2d_bytes_per_step": 2 * sol.info["vec_rows"] * 8,   # load vector f and b
+                "d2h_bytes_per_step": sol.info["n_nodes"] * 8},       # phi
+    }
+
+
+def _roofline(sol, prec, name):
+    ms = sol.profile_spmv(20, prec=prec)
+    nbytes = sol.spmv_bytes(prec)
+    peak, kind = _peaks()
+    achieved = nbytes / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4),
+            "traffic": _traffic_per_launch(sol.info["n_local"], "fp32" if prec else "fp64"),
+            "kernel": name, "peak_kind": f"{kind} hbm_gbs (copy)", "ms_per_launch": round(ms, 5),
+            "algorithmic_bytes": nbytes}
+
+
+def run_ours(args):
     import torch
 
     import gen
@@ -223,90 +290,84 @@ def run_ours(args):
         b.build()
         pkg.load()
 
-    prob = gen.workload(WORKLOAD)
-    stream = torch.cuda.current_stream()
-    sol = pkg.Solver.from_problem(prob, p=P_ROBIN, inner_rtol=INNER_RTOL, max_outer=5000)
-    phi = torch.zeros(sol.info["n_nodes"], dtype=torch.float64, device="cuda")
-
     def barrier():
         if ws > 1:
             torch.distributed.barrier()
 
-    for _ in range(max(args.warmup, 1)):
-        sol.solve(RTOL, phi=phi)
-    st = sol.stats()
-    n_outer, n_cg = st["n_outer"], st["n_cg_steps"]
-    launches_per_step = st["n_launches"]
-
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier()
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        launches = 0
-        for _ in range(args.steps):
-            _, it, rel = sol.solve(RTOL, phi=phi)
-            launches += sol.stats()["n_launches"]
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    clocks = clk.summary()
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = ws * prob.n_dofs / (ms_max / 1e3)
-
-    # end to end through the public API from host buffers: new density in,
-    # solution out to pinned host memory, every step
-    phi_host = torch.empty(sol.info["n_nodes"], dtype=torch.float64, pin_memory=True)
-    drho = np.ascontiguousarray(prob.drho)
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        sol.set_density(drho)
-        sol.solve(RTOL, phi=phi)
-        phi_host.copy_(phi, non_blocking=True)
-        torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
-    e2e = {"value": ws * prob.n_dofs / float(te.item()), "unit": "DOF/s",
-           "h2d_bytes_per_step": 2 * sol.info["vec_rows"] * 8,   # load vector f and b
-           "d2h_bytes_per_step": sol.info["n_nodes"] * 8}        # phi
-
-    # roofline of the dominant kernel (batched SELL SpMV), CUDA events
-    spmv_ms = sol.profile_spmv(20)
-    spmv_bytes = sol.spmv_bytes()
-    peak, peak_kind = _peaks()
-    achieved = spmv_bytes / (spmv_ms / 1e3) / 1e9
-    traffic = _traffic_per_launch(sol.info["n_local"])
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "k_spmv (batched SELL-32 FP64 SpMV, all 64 subdomains)",
-                "peak_kind": f"{peak_kind} hbm_gbs (copy)", "ms_per_launch": round(spmv_ms, 5),
-                "algorithmic_bytes": spmv_bytes}
-
-    line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    prob = gen.workload(WORKLOAD)
+    use_graph = 0 if args.launch == "host" else 1
+    note = "one CUDA graph per solve" if use_graph else "host-driven launches (profiling mode)"
+    res = {}
+    sols = {}
+    for prec in (["mixed", "fp64", "fp64_refine"] if args.prec == "both" else [args.prec]):
+        sol = pkg.Solver.from_problem(prob, p=P_ROBIN, inner_rtol=INNER_RTOL, max_outer=5000,
+                                      prec=prec, mixed_inner_rtol=MIXED_INNER_RTOL, use_graph=use_graph)
+        sols[prec] = sol
+        res[prec] = _measure(sol, prob, args, ws, local, barrier, note)
+        res[prec]["setup_s"] = round(sol.info["setup_seconds"], 2)
+    head = "mixed" if "mixed" in res else "fp64"
+    h = res[head]
+    line = {"metric": METRIC, "value": h["value"], "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inner CG + f64 refinement" if head == "mixed" else "f64",
+            "data": "synthetic",
             "config": {"workload": _workload_desc(prob, P_ROBIN),
+                       "precision": (f"mixed: FP32 subdomain CG to {MIXED_INNER_RTOL:g} of the FP64 defect, "
+                                     "FP64 defect, exchange and stop test" if head == "mixed" else "FP64"),
                        "l2": "inputs larger than L2 (1.6 GB of subdomain matrices), no flush",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
-            "gpu_launches": int(launches),
-            "schwarz_iterations": n_outer, "cg_steps_per_solve": n_cg,
-            "launches_per_step": int(launches_per_step),
-            "setup_s": round(sol.info["setup_seconds"], 2),
-            "e2e": e2e, "roofline": roofline, "clocks": clocks}
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
+                       "launch": h["launch_mode"]},
+            "gpu_launches": h["gpu_launches"], "schwarz_iterations": h["schwarz_iterations"],
+            "cg_steps_per_solve": h["cg_steps_per_solve"], "relres": h["relres"],
+            "setup_s": h["setup_s"], "e2e": h["e2e"], "clocks": h["clocks"]}
+    if head == "mixed":
+        line["roofline"] = _roofline(sols["mixed"], 1, "k_cg_spmv<float> (batched SELL-32 FP32 SpMV, 64 subdomains)")
+    else:
+        line["roofline"] = _roofline(sols["fp64"], 0, "k_cg_spmv<double> (batched SELL-32 FP64 SpMV, 64 subdomains)")
+    keys = ("value", "ms_per_step", "schwarz_iterations", "cg_steps_per_solve", "relres", "gpu_launches", "e2e",
+            "clocks", "setup_s")
+    if "fp64" in res and head != "fp64":
+        f = res["fp64"]
+        line["fp64"] = {k: f[k] for k in keys}
+        line["fp64"]["precision"] = f"FP64, subdomain PCG to {INNER_RTOL:g} of ||b_i|| every iteration (Sec. 6)"
+        line["fp64"]["roofline"] = _roofline(sols["fp64"], 0, "k_cg_spmv<double> (batched SELL-32 FP64 SpMV)")
+        line["mixed_speedup_vs_fp64"] = round(h["value"] / f["value"], 3)
+    if "fp64_refine" in res:
+        f = res["fp64_refine"]
+        line["fp64_refine"] = {k: f[k] for k in keys}
+        line["fp64_refine"]["precision"] = (f"FP64, the mixed form's algorithm: subdomain CG to "
+                                            f"{MIXED_INNER_RTOL:g} of each iteration's defect")
+        if head == "mixed":
+            line["mixed_speedup_vs_fp64_refine"] = round(h["value"] / f["value"], 3)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        n_outer = res["fp64"]["schwarz_iterations"] if "fp64" in res else _reference_iterations()
         line["cpu_baseline"] = _cpu_baseline(prob, P_ROBIN, n_outer)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def profile_iteration(args):
+    """One Schwarz iteration of the bench workload (a few hundred kernel
+    launches), in the precision and launch mode given."""
+    import torch
+
+    import gen
+    import paper_2112_03851_gb300 as pkg
+    torch.cuda.set_device(0)
+    prob = gen.workload(args.workload or WORKLOAD)
+    prec = "mixed" if args.prec == "both" else args.prec
+    sol = pkg.Solver.from_problem(prob, p=P_ROBIN, inner_rtol=INNER_RTOL, max_outer=5000, prec=prec,
+                                  mixed_inner_rtol=MIXED_INNER_RTOL,
+                                  use_graph=0 if args.launch == "host" else 1)
+    sol.reset()
+    hist = sol.iterate(1)
+    st = sol.stats()
+    print(json.dumps({"profile_iteration": args.workload or WORKLOAD, "prec": prec, "relres": float(hist[0]),
+                      **st}), flush=True)
     return 0
 
 
@@ -317,7 +378,17 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", choices=("both", "mixed", "fp64"), default="both")
+    ap.add_argument("--workload", default=None,
+                    help="profiling runs only: another named workload (e.g. layered48)")
+    ap.add_argument("--launch", choices=("graph", "host"), default="graph",
+                    help="host: launch the same kernels one by one (for ncu, which cannot attribute "
+                         "kernels inside graphs with conditional nodes)")
+    ap.add_argument("--profile-iteration", action="store_true",
+                    help="set up the workload, run one Schwarz iteration and exit (for ncu captures)")
     args = ap.parse_args(argv)
+    if args.profile_iteration:
+        return profile_iteration(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -63,7 +63,14 @@ typedef enum {
 
 typedef enum {
     OSM_FP64 = 0,   /* every step in FP64 */
-    OSM_MIXED = 1   /* FP32 subdomain CG inside FP64 refinement (see osm_opts) */
+    OSM_MIXED = 1,  /* per Schwarz iteration and subdomain: FP64 defect d = b - A u, one
+                       FP32 CG solve of A e = d from e = 0 (FP32 matrix values, FP32
+                       vectors and accumulation, FP64 dot products) to
+                       ||r|| <= mixed_inner_rtol ||d||, then u += e in FP64; the Robin
+                       exchange and the stop test stay FP64 */
+    OSM_FP64_REFINE = 2 /* the OSM_MIXED algorithm in FP64: FP64 CG warm-started from u_i,
+                           stopped at ||r|| <= mixed_inner_rtol times its initial residual
+                           (the defect), subdomains whose defect meets inner_rtol skipped */
 } osm_precision;
 
 typedef struct {
@@ -158,18 +165,61 @@ osm_status osm_set_robin_sub(osm_handle h, const double *p_sub);
 osm_status osm_solve(osm_handle h, double rtol, double *phi, int32_t *iters, double *relres);
 
 /*
- * Batched stochastic evaluation of Robin parameters (Sec. 4): n_p candidate
- * values p_host[k] > 0 (host) are run as one batched Schwarz solve sharing
- * the subdomain stiffness matrices, each from u = 0 with its own state and
- * convergence mask, to rtol or max_outer iterations.  iters_host /
- * relres_host (host, n_p each) receive the Schwarz iteration count and final
- * relative residual per candidate; best_idx (host) the fastest-converging
- * candidate (fewest iterations among those that reached rtol, ties to the
- * lower residual, then the smaller p; -1 if none converged).
+ * Batched stochastic evaluation of Robin parameters (Sec. 4): the n_p
+ * candidate values p_host[k] > 0 (host) run the FP64 Schwarz solve of
+ * osm_solve in batches of up to 32 candidates that share the subdomain
+ * stiffness matrices K_i (one pass over K_i serves every candidate of the
+ * batch), each from u = 0 with its own iterate, Robin data, subdomain CG
+ * scalars and convergence mask, until its own relative residual reaches rtol
+ * or max_outer iterations pass.  iters_host / relres_host (host, n_p each)
+ * receive each candidate's Schwarz iteration count and final relative
+ * residual; best_idx (host) the fastest-converging candidate: fewest
+ * iterations among those that reached rtol, ties to the lower residual, then
+ * the smaller p; -1 if none converged (the call then returns OSM_E_NOCONV
+ * with the outputs written).  A candidate's result does not depend on the
+ * other candidates of its batch.  The first call allocates the batch buffers
+ * (about 8 x 32 vectors); the handle's own Robin parameters are restored
+ * before the call returns.
  */
 osm_status osm_sample_p(osm_handle h, int32_t n_p, const double *p_host, double rtol,
                         int32_t max_outer, int32_t *iters_host, double *relres_host,
                         int32_t *best_idx);
+
+/* ----------------------------------------------------------------------
+ * Adjoint gradient of a surface-gravity misfit.  The paper's forward model
+ * (Sec. 2, solved as in Sec. 3) is differentiated; the paper itself has no
+ * gradient.  With f = 4 pi G F drho (F_ae = int_e phi_a) and K phi = f:
+ *   g = B phi (B: d/dz of the Q2 interpolant of the element holding each
+ *   station), J = 1/2 sum_s (g_s - g_obs,s)^2,
+ *   dJ/d drho = 4 pi G F^T w with K w = B^T (g - g_obs),
+ * w computed by one more Schwarz solve with the same p and precision.
+ * ---------------------------------------------------------------------- */
+
+/* Replace the density from a device array (nx*ny*nz, x-fastest); the load
+ * is assembled on the GPU (node-centric, fixed summation order). */
+osm_status osm_set_density_dev(osm_handle h, const double *drho);
+
+/* Stations (host, n_st x 3 coordinates inside the mesh).  A station on an
+ * element boundary belongs to the element on its upper side in that
+ * direction, except on the upper mesh boundary (e.g. surface stations at the
+ * top face), where it belongs to the element below. */
+osm_status osm_set_stations(osm_handle h, int32_t n_st, const double *xyz);
+
+/* g = B phi for a full-grid field phi (device), g device (n_st). */
+osm_status osm_gravity(osm_handle h, const double *phi, double *g);
+
+/* Vector-Jacobian product of phi(drho): given v = dL/dphi (device, full node
+ * grid; Dirichlet entries ignored), solve K w = v by the Schwarz method to
+ * rtol and write dL/d drho = 4 pi G F^T w (device, nx*ny*nz).  The handle's
+ * load is kept; its iterates are overwritten. */
+osm_status osm_potential_vjp(osm_handle h, double rtol, const double *v, double *dL_drho);
+
+/* Forward solve, misfit and adjoint gradient: J (host), dJ_drho (device,
+ * nx*ny*nz), dJ_dp (host, may be NULL).  g_obs: device, n_st.  The
+ * converged solution is the Galerkin solution for every p > 0, so the exact
+ * dJ/dp of the converged map is 0; *dJ_dp receives that value. */
+osm_status osm_grad(osm_handle h, double rtol, const double *g_obs, double *J, double *dJ_drho,
+                    double *dJ_dp);
 
 /* SplitMix64 (Steele, Lea & Flood 2014) log-uniform samples in [lo, hi]:
  * p = exp(log lo + u (log hi - log lo)), u = (x >> 11) * 2^-53, x the k-th
@@ -177,12 +227,43 @@ osm_status osm_sample_p(osm_handle h, int32_t n_p, const double *p_host, double 
 osm_status osm_log_uniform_p(uint64_t seed, int32_t n, double lo, double hi, double *p_host);
 
 /* ----------------------------------------------------------------------
+ * Independent problems in one handle: every instance (its own mesh,
+ * density, decomposition and Robin parameter) runs the Schwarz solve of
+ * osm_solve; all instances' subdomains share every kernel launch of one
+ * CUDA graph, and an instance that has converged is frozen while the others
+ * continue.  Instance i's nodes occupy [off[i], off[i+1]) of node-indexed
+ * arrays (osm_batch_info), each instance's grid x-fastest as usual.
+ * Gradient, stations, osm_set_density* and osm_sample_p need a single-problem
+ * handle (OSM_E_STATE otherwise).
+ * ---------------------------------------------------------------------- */
+
+/* meshes, decs: host arrays of n_inst descriptors; drho: host array of n_inst
+ * host pointers (nx*ny*nz each).  Same errors and *out rule as osm_setup. */
+osm_status osm_setup_batch(int32_t n_inst, const osm_mesh *meshes, const double *const *drho,
+                           const osm_decomp *decs, const osm_opts *opts, void *cuda_stream,
+                           osm_handle *out);
+
+/* n_inst (host) and, if node_offsets != NULL, the n_inst + 1 node offsets. */
+osm_status osm_batch_info(osm_handle h, int32_t *n_inst, int64_t *node_offsets);
+
+/* One Robin parameter per instance (host, n_inst values > 0). */
+osm_status osm_set_robin_inst(osm_handle h, const double *p_inst);
+
+/* Solve every instance from zero to its own relative residual rtol.  phi:
+ * device, total node count (may be NULL); iters / relres: host, n_inst each
+ * (may be NULL).  OSM_E_NOCONV if an instance reached max_outer. */
+osm_status osm_solve_batch(osm_handle h, double rtol, double *phi, int32_t *iters, double *relres);
+
+/* ----------------------------------------------------------------------
  * Step-level entry points (used by the parity tests; same conventions).
  * ---------------------------------------------------------------------- */
 
 /* y = A x per subdomain with x, y in the canonical local layout (device,
  * n_local doubles each).  op 0: A_i = K_i + p_i M_Gi (the Robin matrix);
- * op 1: A_i = K_i (Neumann stiffness). */
+ * op 1: A_i = K_i (Neumann stiffness); op 2 (OSM_MIXED handles only, else
+ * OSM_E_STATE): the FP32 Robin matrix of the mixed inner solve applied to x
+ * rounded to FP32, with FP32 accumulation, returned widened to FP64.  This
+ * call uses the inner solve's work vectors. */
 osm_status osm_apply(osm_handle h, int32_t op, const double *x, double *y);
 
 /* Zero the subdomain iterates u_i and the Robin data lam. */
@@ -227,12 +308,14 @@ osm_status osm_host_face_system(const osm_mesh *mesh, const double *drho, const 
                                 int32_t face, int64_t *n, int64_t *nnz, int32_t *node,
                                 int64_t *rowptr, int32_t *col, double *val);
 
-/* Time the batched SELL SpMV kernel alone: `reps` back-to-back launches of
- * y = A x over every subdomain (the operator of the CG step) between two CUDA
- * events on the handle's stream, after one untimed launch.  *ms receives the
- * mean time per launch in milliseconds (host).  The solver state is not
- * changed. */
-osm_status osm_profile_spmv(osm_handle h, int32_t reps, double *ms);
+/* Time the batched SELL SpMV kernel alone: y = A x over every subdomain
+ * (the operator of the CG step).  prec 0: FP64 values and vectors; prec 1:
+ * the FP32 operator of the mixed inner solve (OSM_MIXED handles only, else
+ * OSM_E_STATE).  After 20 untimed launches, 5 trials of `reps` back-to-back
+ * launches are timed with CUDA events on the handle's stream; *ms receives
+ * the median time per launch in milliseconds (host).  Uses the stop test's
+ * and the inner solve's work vectors; the iterates are not changed. */
+osm_status osm_profile_spmv(osm_handle h, int32_t prec, int32_t reps, double *ms);
 
 /*
  * y = A x exactly as osm_apply computes it, but without any device

@@ -349,3 +349,90 @@ class Schwarz:
     def set_global_rhs(self, fG):
         fG = _f64(fG)
         lib().orc_sz_set_global_rhs(self._h, _ptr(fG))
+
+
+# ------------------------------------------------------------- gradient ----
+# Surface-gravity misfit J = 1/2 ||B phi - g_obs||^2 with K phi = F drho
+# (F: 4 pi G times the element integrals of the basis functions) and its
+# gradient dJ/d drho = F^T K^-1 B^T (B phi - g_obs), written from these
+# definitions with the oracle's own basis, element routine and PCG.
+
+def _locate(c, v):
+    """Element holding coordinate v: the upper-side element on an element
+    boundary, the last element on the upper mesh boundary."""
+    e = int(np.searchsorted(c, v, side="right")) - 1
+    return min(max(e, 0), len(c) - 2)
+
+
+def station_matrix(G, stations):
+    """B (n_st x unknowns of G): d/dz of the Q2 interpolant at each station;
+    Dirichlet nodes (phi = 0) are dropped."""
+    import scipy.sparse as sp
+    NX, NY = 2 * G.nx + 1, 2 * G.ny + 1
+    unk = np.full(G.n_nodes, -1, dtype=np.int64)
+    unk[G.gnode] = np.arange(G.n)
+    rows, cols, vals = [], [], []
+    for s, (x, y, z) in enumerate(np.asarray(stations, dtype=np.float64)):
+        ex, ey, ez = _locate(G.xc, x), _locate(G.yc, y), _locate(G.zc, z)
+        hx, hy, hz = G.xc[ex + 1] - G.xc[ex], G.yc[ey + 1] - G.yc[ey], G.zc[ez + 1] - G.zc[ez]
+        Lx, _ = basis_1d((x - G.xc[ex]) / hx)
+        Ly, _ = basis_1d((y - G.yc[ey]) / hy)
+        _, dLz = basis_1d((z - G.zc[ez]) / hz)
+        for c in range(3):
+            for b in range(3):
+                for a in range(3):
+                    node = (2 * ex + a) + NX * ((2 * ey + b) + NY * (2 * ez + c))
+                    if unk[node] >= 0:
+                        rows.append(s)
+                        cols.append(unk[node])
+                        vals.append(Lx[a] * Ly[b] * dLz[c] / hz)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(len(stations), G.n))
+
+
+def load_matrix(G):
+    """F (unknowns x elements): F[a, e] = 4 pi G_newton int_e phi_a."""
+    import scipy.sparse as sp
+    NX, NY = 2 * G.nx + 1, 2 * G.ny + 1
+    unk = np.full(G.n_nodes, -1, dtype=np.int64)
+    unk[G.gnode] = np.arange(G.n)
+    cache = {}
+    rows, cols, vals = [], [], []
+    e = 0
+    for ez in range(G.nz):
+        for ey in range(G.ny):
+            for ex in range(G.nx):
+                h = (G.xc[ex + 1] - G.xc[ex], G.yc[ey + 1] - G.yc[ey], G.zc[ez + 1] - G.zc[ez])
+                if h not in cache:
+                    cache[h] = element(*h)[2]
+                w = cache[h]
+                for I in range(27):
+                    a, b, c = I % 3, (I // 3) % 3, I // 9
+                    node = (2 * ex + a) + NX * ((2 * ey + b) + NY * (2 * ez + c))
+                    if unk[node] >= 0:
+                        rows.append(unk[node])
+                        cols.append(e)
+                        vals.append(4.0 * np.pi * G_NEWTON * w[I])
+                e += 1
+    return sp.csr_matrix((vals, (rows, cols)), shape=(G.n, G.nx * G.ny * G.nz))
+
+
+class Misfit:
+    """J(drho) = 1/2 ||B K^-1 F drho - g_obs||^2 on the monolithic system."""
+
+    def __init__(self, xc, yc, zc, stations, tol=1e-14):
+        self.G = GlobalSystem(xc, yc, zc)
+        self.B = station_matrix(self.G, stations)
+        self.F = load_matrix(self.G)
+        self.tol = tol
+
+    def potential(self, drho):
+        u, _, _ = self.G.solve(self.F @ np.asarray(drho, dtype=np.float64), tol=self.tol)
+        return u
+
+    def gravity(self, drho):
+        return self.B @ self.potential(drho)
+
+    def value_and_grad(self, drho, g_obs):
+        r = self.gravity(drho) - g_obs
+        w, _, _ = self.G.solve(self.B.T @ r, tol=self.tol)
+        return 0.5 * float(r @ r), self.F.T @ w

@@ -13,15 +13,16 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libosm.so")
 
 OSM_OK, OSM_E_ARG, OSM_E_CUDA, OSM_E_NOMEM, OSM_E_NOCONV, OSM_E_BREAKDOWN, OSM_E_STATE, OSM_E_TIMEOUT = range(8)
-OSM_FP64, OSM_MIXED = 0, 1
+OSM_FP64, OSM_MIXED, OSM_FP64_REFINE = 0, 1, 2
 
 EXPORTED = (
     "osm_default_opts", "osm_setup", "osm_info", "osm_set_density", "osm_set_robin",
     "osm_set_robin_sub", "osm_solve", "osm_sample_p", "osm_log_uniform_p", "osm_apply",
-    "osm_reset", "osm_iterate", "osm_get_local", "osm_get_lambda", "osm_set_lambda",
-    "osm_apply_noalloc", "osm_inner_iters", "osm_stats", "osm_host_local_system", "osm_host_face_system", "osm_profile_spmv",
-    "osm_status_string",
-    "osm_last_error", "osm_destroy",
+    "osm_apply_noalloc", "osm_reset", "osm_iterate", "osm_get_local", "osm_get_lambda",
+    "osm_set_lambda", "osm_inner_iters", "osm_stats", "osm_set_density_dev", "osm_set_stations",
+    "osm_gravity", "osm_potential_vjp", "osm_grad", "osm_host_local_system", "osm_host_face_system",
+    "osm_profile_spmv", "osm_status_string", "osm_last_error", "osm_destroy", "osm_setup_batch",
+    "osm_batch_info", "osm_set_robin_inst", "osm_solve_batch",
 )
 
 
@@ -92,9 +93,18 @@ def load():
         "osm_set_lambda": (C.c_int, [vp, vp]),
         "osm_inner_iters": (C.c_int, [vp, vp]),
         "osm_stats": (C.c_int, [vp, vp]),
+        "osm_set_density_dev": (C.c_int, [vp, vp]),
+        "osm_set_stations": (C.c_int, [vp, i32, vp]),
+        "osm_gravity": (C.c_int, [vp, vp, vp]),
+        "osm_potential_vjp": (C.c_int, [vp, d, vp, vp]),
+        "osm_grad": (C.c_int, [vp, d, vp, vp, vp, vp]),
         "osm_host_local_system": (C.c_int, [vp, vp, vp, d, i32, vp, vp, vp, vp, vp, vp]),
         "osm_host_face_system": (C.c_int, [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]),
-        "osm_profile_spmv": (C.c_int, [vp, i32, vp]),
+        "osm_profile_spmv": (C.c_int, [vp, i32, i32, vp]),
+        "osm_setup_batch": (C.c_int, [i32, vp, vp, vp, vp, vp, vp]),
+        "osm_batch_info": (C.c_int, [vp, vp, vp]),
+        "osm_set_robin_inst": (C.c_int, [vp, vp]),
+        "osm_solve_batch": (C.c_int, [vp, d, vp, vp, vp]),
         "osm_status_string": (C.c_char_p, [C.c_int]),
         "osm_last_error": (C.c_char_p, [vp]),
         "osm_destroy": (None, [vp]),
@@ -146,7 +156,7 @@ def default_opts(**kw) -> OsmOpts:
     load().osm_default_opts(C.byref(o))
     for k, v in kw.items():
         if k == "prec" and isinstance(v, str):
-            v = {"fp64": OSM_FP64, "mixed": OSM_MIXED}[v]
+            v = {"fp64": OSM_FP64, "mixed": OSM_MIXED, "fp64_refine": OSM_FP64_REFINE}[v]
         setattr(o, k, v)
     return o
 
@@ -272,6 +282,43 @@ class Solver:
         lam = lam.contiguous()
         self._check(load().osm_set_lambda(self._h, _dptr(lam)))
 
+    # ------------------------------------------------------ adjoint gradient
+    @property
+    def n_elements(self):
+        return (len(self._in.xc) - 1) * (len(self._in.yc) - 1) * (len(self._in.zc) - 1)
+
+    def set_density_dev(self, drho):
+        """Density from a device tensor (float64, nx*ny*nz); load built on the GPU."""
+        drho = drho.detach().to(dtype=self._torch.float64).contiguous()
+        assert drho.numel() == self.n_elements and drho.is_cuda
+        self._check(load().osm_set_density_dev(self._h, _dptr(drho)))
+
+    def set_stations(self, xyz):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64).reshape(-1, 3)
+        self._check(load().osm_set_stations(self._h, len(xyz), _ptr(xyz)))
+        self.n_stations = len(xyz)
+
+    def gravity(self, phi):
+        g = self._zeros(self.n_stations)
+        self._check(load().osm_gravity(self._h, _dptr(phi.contiguous()), _dptr(g)))
+        return g
+
+    def potential_vjp(self, v, rtol=1e-8):
+        """dL/d drho for v = dL/dphi (device, full node grid), by one adjoint solve."""
+        v = v.detach().to(dtype=self._torch.float64).contiguous()
+        grad = self._zeros(self.n_elements)
+        self._check(load().osm_potential_vjp(self._h, float(rtol), _dptr(v), _dptr(grad)))
+        return grad
+
+    def grad(self, g_obs, rtol=1e-8):
+        """(J, dJ/d drho, dJ/dp) of J = 1/2 ||B phi - g_obs||^2 at the current density."""
+        g_obs = g_obs.detach().to(dtype=self._torch.float64).contiguous()
+        J = C.c_double()
+        dp = C.c_double()
+        grad = self._zeros(self.n_elements)
+        self._check(load().osm_grad(self._h, float(rtol), _dptr(g_obs), C.byref(J), _dptr(grad), C.byref(dp)))
+        return J.value, grad, dp.value
+
     def stats(self):
         st = OsmStats()
         self._check(load().osm_stats(self._h, C.byref(st)))
@@ -282,17 +329,20 @@ class Solver:
         self._check(load().osm_inner_iters(self._h, _ptr(it)))
         return it
 
-    def profile_spmv(self, reps=20):
-        """Mean time (ms) of one batched SELL SpMV launch, CUDA events."""
+    def profile_spmv(self, reps=20, prec=0):
+        """Median time (ms) of one batched SELL SpMV launch (CUDA events);
+        prec 0: FP64, 1: the FP32 operator of the mixed inner solve."""
         ms = C.c_double()
-        self._check(load().osm_profile_spmv(self._h, int(reps), C.byref(ms)))
+        self._check(load().osm_profile_spmv(self._h, int(prec), int(reps), C.byref(ms)))
         return ms.value
 
-    def spmv_bytes(self):
-        """Algorithmic bytes of one SpMV: nnz (8 B value + 4 B column), 8 B per
-        slice offset, the input vector read once and the output written once."""
+    def spmv_bytes(self, prec=0):
+        """Algorithmic bytes of one SpMV: per nonzero the value (8 B FP64 or
+        4 B FP32) and its 4 B column, 8 B per slice offset, the input vector
+        read once and the output written once."""
         i = self.info
-        return i["nnz"] * 12 + i["n_slices"] * 8 + i["n_local"] * 16
+        vb = 8 if prec == 0 else 4
+        return i["nnz"] * (vb + 4) + i["n_slices"] * 8 + i["n_local"] * 2 * vb
 
     def sample_p(self, p_values, rtol=1e-8, max_outer=None):
         p = np.ascontiguousarray(p_values, dtype=np.float64)
@@ -304,6 +354,63 @@ class Solver:
         self._check(load().osm_sample_p(self._h, n, _ptr(p), float(rtol), mo, _ptr(iters), _ptr(rel),
                                         C.byref(best)), (OSM_E_NOCONV,))
         return iters, rel, best.value
+
+
+class BatchSolver(Solver):
+    """Several independent problems in one handle (one CUDA graph per solve).
+
+    ``problems``: objects with xc, yc, zc, drho, cx, cy, cz (and p)."""
+
+    def __init__(self, problems, p=None, stream=None, **opts):
+        import torch
+        L = load()
+        self._torch = torch
+        self._ins = [_Inputs(q.xc, q.yc, q.zc, q.drho, q.cx, q.cy, q.cz) for q in problems]
+        self._in = self._ins[0]
+        n = len(problems)
+        meshes = (OsmMesh * n)(*[i.mesh for i in self._ins])
+        decs = (OsmDecomp * n)(*[i.dec for i in self._ins])
+        dptrs = (C.c_void_p * n)(*[_ptr(i.drho).value for i in self._ins])
+        self.opts = default_opts(**opts)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        h = C.c_void_p()
+        st = L.osm_setup_batch(n, meshes, dptrs, decs, C.byref(self.opts), C.c_void_p(stream.cuda_stream),
+                               C.byref(h))
+        self._h = h
+        if st != OSM_OK:
+            msg = L.osm_last_error(h).decode() if h.value else ""
+            self.close()
+            raise OsmError(st, msg)
+        info = OsmInfo()
+        L.osm_info(h, C.byref(info))
+        self.info = {k: getattr(info, k) for k, _ in OsmInfo._fields_}
+        self.n_inst = n
+        off = np.zeros(n + 1, dtype=np.int64)
+        ni = C.c_int32()
+        L.osm_batch_info(h, C.byref(ni), _ptr(off))
+        self.node_offsets = off
+        ps = [q.p for q in problems] if p is None else (np.broadcast_to(p, (n,)))
+        self.set_robin_inst(ps)
+
+    def set_robin_inst(self, p_inst):
+        p_inst = np.ascontiguousarray(p_inst, dtype=np.float64)
+        self._check(load().osm_set_robin_inst(self._h, _ptr(p_inst)))
+
+    def solve(self, rtol=1e-8, phi=None, allow_noconv=False):
+        """Returns (phi of all instances concatenated, iterations[n], relres[n])."""
+        if phi is None:
+            phi = self._zeros(self.info["n_nodes"])
+        it = np.zeros(self.n_inst, dtype=np.int32)
+        rel = np.zeros(self.n_inst)
+        allow = (OSM_E_NOCONV,) if allow_noconv else ()
+        self._check(load().osm_solve_batch(self._h, float(rtol), _dptr(phi), _ptr(it), _ptr(rel)), allow)
+        return phi, it, rel
+
+    def instance_phi(self, phi, i):
+        return phi[int(self.node_offsets[i]):int(self.node_offsets[i + 1])]
 
 
 def log_uniform_p(seed: int, n: int, lo: float, hi: float) -> np.ndarray:
@@ -348,3 +455,48 @@ def host_face_system(xc, yc, zc, drho, cx, cy, cz, face):
     v = np.zeros(nnz.value)
     L.osm_host_face_system(*args, C.byref(n), C.byref(nnz), _ptr(node), _ptr(rp), _ptr(ci), _ptr(v))
     return node, sp.csr_matrix((v, ci, rp), shape=(n.value, n.value))
+
+
+def _autograd():
+    import torch
+
+    class GravityPotential(torch.autograd.Function):
+        """phi(drho) through the Schwarz solve; backward = one adjoint solve."""
+
+        @staticmethod
+        def forward(ctx, drho, solver, rtol):
+            solver.set_density_dev(drho)
+            phi, _, _ = solver.solve(rtol)
+            ctx.solver, ctx.rtol = solver, rtol
+            return phi
+
+        @staticmethod
+        def backward(ctx, gphi):
+            return ctx.solver.potential_vjp(gphi, ctx.rtol), None, None
+
+    class GravityMisfit(torch.autograd.Function):
+        """J(drho) = 1/2 ||B phi(drho) - g_obs||^2; gradient by the adjoint solve."""
+
+        @staticmethod
+        def forward(ctx, drho, g_obs, solver, rtol):
+            solver.set_density_dev(drho)
+            J, grad, _ = solver.grad(g_obs, rtol)
+            ctx.save_for_backward(grad)
+            return torch.tensor(J, dtype=torch.float64, device=drho.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            (grad,) = ctx.saved_tensors
+            return gJ * grad, None, None, None
+
+    return GravityPotential, GravityMisfit
+
+
+def gravity_potential(drho, solver, rtol=1e-8):
+    """Differentiable phi(drho) (torch.autograd)."""
+    return _autograd()[0].apply(drho, solver, rtol)
+
+
+def gravity_misfit(drho, g_obs, solver, rtol=1e-8):
+    """Differentiable misfit J(drho) = 1/2 ||B phi - g_obs||^2 (torch.autograd)."""
+    return _autograd()[1].apply(drho, g_obs, solver, rtol)

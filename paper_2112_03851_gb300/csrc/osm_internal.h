@@ -54,6 +54,7 @@ struct HostProblem {
   std::vector<int64_t> slice_off;
   std::vector<int32_t> cols;          // subdomain-local row index (internal order)
   std::vector<double> vals;
+  std::vector<float> vals32;          // FP32 copy in the column (quad) layout, mixed mode only
 
   std::vector<int32_t> tile_sub;      // tile -> subdomain
   std::vector<int32_t> row_sub;       // not stored on device; per vector row
@@ -73,6 +74,7 @@ struct HostProblem {
   std::vector<double> im_val;         // M_Gi value
   std::vector<int64_t> im_pos;        // position of the entry in the SELL value array
   std::vector<double> im_kval;        // K_i value at that position
+  std::vector<int64_t> im_pos32;      // position in the FP32 value array
 
   // Faces (canonical face layout) and their mass matrices.
   int nface = 0;
@@ -88,12 +90,31 @@ struct HostProblem {
   // Copies of each node of the full grid (vector rows, subdomain order).
   std::vector<int32_t> cp_ptr;        // n_nodes + 1
   std::vector<int32_t> cp_idx;
+
+  // Independent problems (instances) solved together: instance i owns
+  // subdomains [inst_sub0[i], inst_sub0[i+1]) and nodes [inst_node0[i],
+  // inst_node0[i+1]) of the concatenated node grids.  A single problem is
+  // one instance.
+  int n_inst = 1;
+  std::vector<int32_t> sub_inst;      // subdomain -> instance
+  std::vector<int32_t> inst_sub0;     // n_inst + 1
+  std::vector<int64_t> inst_node0;    // n_inst + 1
+  // Blocks of the node-wise stop-test kernels: block b covers nodes
+  // [rblock_node0[b], rblock_node0[b+1]) of instance rblock_inst[b].
+  std::vector<int32_t> rblock_inst;
+  std::vector<int64_t> rblock_node0;
+  std::vector<int32_t> inst_rblock0;  // n_inst + 1: first residual block of each instance
 };
+
+// Concatenate independently built problems into one batched problem.
+std::string merge_problems(std::vector<HostProblem>& parts, HostProblem& out);
+// Fill the instance / residual-block tables of a single problem.
+void single_instance_tables(HostProblem& hp);
 
 // Build everything on the host.  Returns an empty string on success, else
 // the reason of the failure.
 std::string build_host_problem(const osm_mesh& mesh, const double* drho, const osm_decomp& dec,
-                               HostProblem& hp);
+                               HostProblem& hp, bool want_fp32 = false);
 
 // Rebuild the load vector (per vector row) for a new density.
 void build_load(const HostProblem& hp, const double* drho, std::vector<double>& f);
@@ -128,10 +149,11 @@ struct DevCtl {
   int32_t total_inner;    // batched CG steps summed over the Schwarz iterations
   int32_t pad0;
   double relres;          // last stop-test value
+  double tau2_outer;      // mixed mode: FP64 local tolerance^2 that skips a correction
   unsigned long long t_start_ns;  // %globaltimer at the first kernel of the call
   unsigned long long t_limit_ns;  // wall-clock budget of the call
   int32_t stop;           // set once the budget is exhausted: both loops end
-  int32_t pad1;
+  int32_t running;        // instances not yet done after the last stop test
   unsigned gcnt_b;        // global last-block counters
   unsigned gcnt_i;
   unsigned gcnt_r;
@@ -146,6 +168,7 @@ struct DevProblem {
   const int32_t* tile_sub;
   const int64_t* sub_tile0;   // n_sub + 1
   int64_t n_tiles;
+  int32_t n_sub;
   // vectors (vec_rows each)
   double *x, *r, *z, *p, *q, *b, *f, *dinv, *w, *y;
   // per subdomain
@@ -174,18 +197,100 @@ struct DevProblem {
   double* rpart2;
   int64_t n_rblocks;
   double* hist;         // residual history (max_outer)
+  // instances
+  int32_t n_inst;
+  const int32_t *sub_inst, *rblock_inst, *inst_rblock0;
+  const int64_t* rblock_node0;
+  int32_t* inst_done;   // instance converged (or out of iterations) in this solve
+  int32_t* inst_iters;  // Schwarz iterations of each instance
+  double* inst_relres;  // last stop-test value of each instance
+  unsigned* inst_cnt;   // per-instance residual tickets
+  // mixed precision (null in FP64 mode)
+  float* vals32;
+  const int64_t* im_pos32;
+  float *x32, *r32, *z32, *p32, *q32, *dinv32;
   DevCtl* ctl;
   const int32_t* can2vec;
   int64_t n_local;
+};
+
+// Batched evaluation of Robin parameters (osm_sample_p): up to
+// kSampleWidth candidates run as one Schwarz solve.  Every vector holds the
+// candidates' values of a row contiguously ([row][kSampleWidth]) so that a
+// warp's 32 lanes are the 32 candidates.
+constexpr int kSampleWidth = 32;
+constexpr int kNodeBlocks = 1024;   // blocks of the node-wise kernels (grid-stride)
+
+struct DevSample {
+  double* psamp;                        // [kSampleWidth]
+  double *x, *r, *z, *pd, *q, *b, *w, *y;  // [vec_rows][kSampleWidth]
+  double* lam;                          // [2 n_fent][kSampleWidth]
+  double *part0, *part1, *part2;        // [n_tiles][kSampleWidth]
+  double *rho, *alpha, *beta, *bb, *rr; // [n_sub][kSampleWidth]
+  int32_t *active, *iters;              // [n_sub][kSampleWidth]
+  int32_t* done;                        // [kSampleWidth]
+  int32_t* outer_iters;                 // [kSampleWidth]
+  double* relres;                       // [kSampleWidth]
+  double *rpart, *rpart2;               // [kNodeBlocks][kSampleWidth]
+  const int32_t* row_irow;              // [vec_rows]: interface-row index or -1
+};
+
+// Adjoint gradient data (osm_adjoint.cu): device copies of the mesh and the
+// subdomain element boxes, the row -> node map, and the station operator B
+// (one row per station: 27 node ids and weights of d/dz of the Q2
+// interpolant of the station's element).
+struct DevAdjoint {
+  const double *xc, *yc, *zc;
+  int32_t nx, ny, nz, NX, NY, NZ;
+  const int32_t* sub_box;     // [n_sub][6]: ex0, ex1, ey0, ey1, ez0, ez1
+  const int32_t* row_node;    // [vec_rows]: full-grid node or -1
+  int32_t n_st;
+  const int32_t* st_node;     // [n_st][27]
+  const double* st_w;         // [n_st][27]
+  double *g, *res;            // [n_st]: B phi, B phi - g_obs
+  double* jpart;              // [kNodeBlocks]
+  double* f_save;             // [vec_rows]: the density load while an adjoint load is in place
+  double* v_nodes;            // [n_nodes]: nodal adjoint load
+};
+
+// CG vectors of one precision.
+template <class T>
+struct CgVec {
+  T *x, *r, *z, *p, *q;
+  const T* dinv;
+  const T* vals;
 };
 
 // Kernel launchers (osm_kernels.cu).  All enqueue on `s` and return the
 // launch error.  `cond` / `use_cond` name the graph conditional to drive.
 cudaError_t launch_set_robin(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_rhs_gather(const DevProblem& d, cudaStream_t s);
-cudaError_t launch_cg_init(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
+cudaError_t launch_cg_init(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond,
+                           int defect_norm = 0);
 cudaError_t launch_cg_iteration(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
+cudaError_t launch_cg_iteration32(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
+cudaError_t launch_cg_init_mixed(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
+cudaError_t launch_mixed_correct(const DevProblem& d, cudaStream_t s);
+cudaError_t launch_apply32(const DevProblem& d, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_spmv_plain32(const DevProblem& d, const float* x, float* y, cudaStream_t s);
 cudaError_t launch_exchange(const DevProblem& d, cudaStream_t s);
+// adjoint gradient (osm_adjoint.cu)
+cudaError_t launch_load_from_density(const DevProblem& d, const DevAdjoint& a, const double* drho, cudaStream_t s);
+cudaError_t launch_station_values(const DevProblem& d, const DevAdjoint& a, const double* phi, const double* g_obs,
+                                  cudaStream_t s);
+cudaError_t launch_misfit(const DevAdjoint& a, double* J_dev, cudaStream_t s);
+cudaError_t launch_stations_transpose(const DevProblem& d, const DevAdjoint& a, cudaStream_t s);
+cudaError_t launch_nodal_load(const DevProblem& d, const DevAdjoint& a, const double* v_nodes, cudaStream_t s);
+cudaError_t launch_density_gradient(const DevProblem& d, const DevAdjoint& a, const double* w_nodes, double* grad,
+                                    cudaStream_t s);
+// batched p evaluation (osm_sample.cu)
+cudaError_t launch_mp_start(const DevProblem& d, const DevSample& m, cudaStream_t s);
+cudaError_t launch_mp_rhs_init(const DevProblem& d, const DevSample& m, cudaStream_t s, unsigned long long cond,
+                               int use_cond);
+cudaError_t launch_mp_cg_iteration(const DevProblem& d, const DevSample& m, cudaStream_t s,
+                                   unsigned long long cond, int use_cond);
+cudaError_t launch_mp_exchange_residual(const DevProblem& d, const DevSample& m, cudaStream_t s,
+                                        unsigned long long cond, int use_cond);
 cudaError_t launch_residual(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
 cudaError_t launch_apply(const DevProblem& d, int op, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_gather_local(const DevProblem& d, const double* vec, double* canon, cudaStream_t s);

@@ -15,103 +15,12 @@
 // cudaGraphSetConditional from that single last block.
 #include <cuda_runtime.h>
 
+#include "osm_device.cuh"
 #include "osm_internal.h"
 
 namespace osm {
 
 namespace {
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Sum NV values over the 256 threads of a block; result valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sm)[kTileSlices]) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    double s = warp_sum(v[k]);
-    if (lane == 0) sm[k][warp] = s;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double s = 0.0;
-#pragma unroll
-      for (int w = 0; w < kTileSlices; ++w) s += sm[k][w];
-      v[k] = s;
-    }
-  }
-}
-
-// Sum of part[t0 .. t0+nt) in a fixed order by one warp (all lanes get it).
-__device__ __forceinline__ double warp_sum_parts(const double* part, int64_t t0, int64_t nt) {
-  const int lane = threadIdx.x & 31;
-  double v = 0.0;
-  for (int64_t k = lane; k < nt; k += 32) v += __ldcg(part + t0 + k);
-  return warp_sum(v);
-}
-
-// One row of a SELL-32 slice: lane `lane` of the warp owning the slice at
-// `off` (width w, multiple of 4).  Matrix data is streamed (evict-first);
-// the gathered vector stays cached.
-__device__ __forceinline__ double sell_row(const int32_t* __restrict__ cols,
-                                           const double* __restrict__ vals, int64_t off, int w,
-                                           int lane, const double* __restrict__ x) {
-  const int4* c4 = reinterpret_cast<const int4*>(cols + off) + lane;
-  const double2* v2 = reinterpret_cast<const double2*>(vals + off) + lane;
-  double acc0 = 0.0, acc1 = 0.0;
-  const int nq = w >> 2;
-#pragma unroll 4
-  for (int q = 0; q < nq; ++q) {
-    const int4 c = __ldcs(c4 + q * 32);
-    const double2 a = __ldcs(v2 + q * 64);
-    const double2 b = __ldcs(v2 + q * 64 + 32);
-    acc0 = fma(a.x, __ldg(x + c.x), acc0);
-    acc1 = fma(a.y, __ldg(x + c.y), acc1);
-    acc0 = fma(b.x, __ldg(x + c.z), acc0);
-    acc1 = fma(b.y, __ldg(x + c.w), acc1);
-  }
-  return acc0 + acc1;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// True (and the stop flag raised, status bit 2) once the call's wall-clock
-// budget is used up.  Called by single threads only.
-__device__ __forceinline__ bool out_of_time(DevCtl* c) {
-  if (c->stop) return true;
-  if (global_ns() - c->t_start_ns > c->t_limit_ns) {
-    c->stop = 1;
-    atomicOr(&c->status, 4);
-    return true;
-  }
-  return false;
-}
-
-// Ticket of the last block: returns true in every thread of the block that
-// finished last among `total` blocks counted on *cnt (and resets it).
-__device__ __forceinline__ bool last_block(unsigned* cnt, unsigned total, bool* flag_sm) {
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    unsigned prev = atomicAdd(cnt, 1u);
-    *flag_sm = (prev == total - 1);
-    if (*flag_sm) *cnt = 0u;
-  }
-  __syncthreads();
-  bool last = *flag_sm;
-  if (last) __threadfence();
-  return last;
-}
 
 // ------------------------------------------------------------------ kernels
 
@@ -121,9 +30,15 @@ __global__ void k_set_robin(DevProblem d) {
   if (k >= d.n_irow) return;
   const int s = d.irow_sub[k];
   const double p = d.psub[s];
-  for (int32_t e = d.im_ptr[k]; e < d.im_ptr[k + 1]; ++e) d.vals[d.im_pos[e]] = d.im_kval[e] + p * d.im_val[e];
+  for (int32_t e = d.im_ptr[k]; e < d.im_ptr[k + 1]; ++e) {
+    const double a = d.im_kval[e] + p * d.im_val[e];
+    d.vals[d.im_pos[e]] = a;
+    if (d.vals32) d.vals32[d.im_pos32[e]] = (float)a;
+  }
   const int32_t row = d.irow[k];
-  d.dinv[row] = 1.0 / (d.kdiag[row] + p * d.irow_mdiag[k]);
+  const double di = 1.0 / (d.kdiag[row] + p * d.irow_mdiag[k]);
+  d.dinv[row] = di;
+  if (d.dinv32) d.dinv32[row] = (float)di;
 }
 
 // b_i = f_i + sum_j lam_ij on interface rows (other rows keep b = f).
@@ -141,18 +56,17 @@ __global__ void k_rhs_gather(DevProblem d) {
   d.b[row] = b;
 }
 
-// CG start from the warm iterate x: r = b - A x, z = D^-1 r, p = z;
-// per subdomain rho = r.z, ||b||^2, ||r||^2 and the active flag.
-__global__ void __launch_bounds__(kTileRows) k_cg_init(DevProblem d, unsigned long long cond, int use_cond) {
+// CG start from the warm iterate x: r = b - A x, z = D^-1 r, p = z, and the
+// tile partials of ||r||^2, ||b||^2 and r.z (finalised by k_fin_init).
+__global__ void __launch_bounds__(kTileRows) k_cg_init(DevProblem d) {
   __shared__ double sm[3][kTileSlices];
-  __shared__ bool flag;
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t slice = tile * kTileSlices + warp;
   const int64_t off = d.slice_off[slice];
   const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
-  const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
+  const int64_t t0 = d.sub_tile0[s];
   const double* xs = d.x + t0 * kTileRows;
   const int64_t row = tile * kTileRows + threadIdx.x;
   const double ax = sell_row(d.cols, d.vals, off, w, lane, xs);
@@ -169,34 +83,13 @@ __global__ void __launch_bounds__(kTileRows) k_cg_init(DevProblem d, unsigned lo
     d.part1[tile] = v[1];
     d.part2[tile] = v[2];
   }
-  if (last_block(&d.st.cnt_i[s], (unsigned)nt, &flag)) {
-    if (warp == 0) {
-      const double rr = warp_sum_parts(d.part0, t0, nt);
-      const double bb = warp_sum_parts(d.part1, t0, nt);
-      const double rz = warp_sum_parts(d.part2, t0, nt);
-      if (lane == 0) {
-        d.st.rr[s] = rr;
-        d.st.bb[s] = bb;
-        d.st.rho[s] = rz;
-        d.st.beta[s] = 0.0;
-        d.st.iters[s] = 0;
-        d.st.status[s] = 0;
-        const int act = !(rr <= d.ctl->tau2 * bb);
-        d.st.active[s] = act;
-        if (act) atomicAdd(&d.ctl->n_active, 1);
-      }
-    }
-  }
-  if (use_cond && last_block(&d.ctl->gcnt_i, gridDim.x, &flag)) {
-    if (threadIdx.x == 0)
-      cudaGraphSetConditional(cond, (atomicAdd(&d.ctl->n_active, 0) > 0 && !out_of_time(d.ctl)) ? 1u : 0u);
-  }
 }
 
-// q = A p and alpha = rho / (p.q) per active subdomain.
-__global__ void __launch_bounds__(kTileRows) k_cg_spmv(DevProblem d) {
+// q = A p and the tile partials of p.q on active subdomains (T = double for
+// the FP64 solve, float for the mixed-precision inner solve; dots in FP64).
+template <class T>
+__global__ void __launch_bounds__(kTileRows) k_cg_spmv(DevProblem d, CgVec<T> v) {
   __shared__ double sm[1][kTileSlices];
-  __shared__ bool flag;
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
   if (!d.st.active[s]) return;
@@ -204,94 +97,206 @@ __global__ void __launch_bounds__(kTileRows) k_cg_spmv(DevProblem d) {
   const int64_t slice = tile * kTileSlices + warp;
   const int64_t off = d.slice_off[slice];
   const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
-  const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
+  const int64_t t0 = d.sub_tile0[s];
   const int64_t row = tile * kTileRows + threadIdx.x;
-  const double q = sell_row(d.cols, d.vals, off, w, lane, d.p + t0 * kTileRows);
-  d.q[row] = q;
-  double v[1] = {d.p[row] * q};
-  block_sum<1>(v, sm);
-  if (threadIdx.x == 0) d.part0[tile] = v[0];
-  if (last_block(&d.st.cnt_a[s], (unsigned)nt, &flag) && warp == 0) {
-    const double pq = warp_sum_parts(d.part0, t0, nt);
-    if (lane == 0) {
-      if (!(pq > 0.0) || !isfinite(pq)) {  // breakdown: stop this subdomain
-        d.st.alpha[s] = 0.0;
-        d.st.status[s] |= 2;
-        atomicOr(&d.ctl->status, 2);
-        d.st.active[s] = 0;
-        atomicSub(&d.ctl->n_active, 1);
-      } else {
-        d.st.alpha[s] = d.st.rho[s] / pq;
-      }
-    }
-  }
+  const T q = sell_row(d.cols, v.vals, off, w, lane, v.p + t0 * kTileRows);
+  v.q[row] = q;
+  double vv[1] = {(double)v.p[row] * (double)q};
+  block_sum<1>(vv, sm);
+  if (threadIdx.x == 0) d.part0[tile] = vv[0];
 }
 
-// x += alpha p, r -= alpha q, z = D^-1 r; then rho, ||r||^2, the stop test
-// ||r|| <= tau ||b|| and beta per subdomain.
-__global__ void __launch_bounds__(kTileRows) k_cg_update(DevProblem d, unsigned long long cond, int use_cond) {
+// x += alpha p, r -= alpha q, z = D^-1 r, and the tile partials of r.z and
+// ||r||^2 (k_fin_beta turns them into rho, the stop test and beta).
+template <class T>
+__global__ void __launch_bounds__(kTileRows) k_cg_update(DevProblem d, CgVec<T> v) {
   __shared__ double sm[2][kTileSlices];
-  __shared__ bool flag;
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
   const int act = d.st.active[s];
   if (act) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
     const int64_t row = tile * kTileRows + threadIdx.x;
-    const double alpha = d.st.alpha[s];
-    const double pr = d.p[row];
-    d.x[row] = fma(alpha, pr, d.x[row]);
-    const double r = fma(-alpha, d.q[row], d.r[row]);
-    const double z = d.dinv[row] * r;
-    d.r[row] = r;
-    d.z[row] = z;
-    double v[2] = {r * z, r * r};
-    block_sum<2>(v, sm);
+    const T alpha = (T)d.st.alpha[s];
+    const T pr = v.p[row];
+    v.x[row] = fma(alpha, pr, v.x[row]);
+    const T r = fma(-alpha, v.q[row], v.r[row]);
+    const T z = v.dinv[row] * r;
+    v.r[row] = r;
+    v.z[row] = z;
+    double vv[2] = {(double)r * (double)z, (double)r * (double)r};
+    block_sum<2>(vv, sm);
     if (threadIdx.x == 0) {
-      d.part1[tile] = v[0];
-      d.part2[tile] = v[1];
-    }
-    if (last_block(&d.st.cnt_b[s], (unsigned)nt, &flag) && warp == 0) {
-      const double rz = warp_sum_parts(d.part1, t0, nt);
-      const double rr = warp_sum_parts(d.part2, t0, nt);
-      if (lane == 0) {
-        const int it = d.st.iters[s] + 1;
-        d.st.iters[s] = it;
-        d.st.rr[s] = rr;
-        if (rr <= d.ctl->tau2 * d.st.bb[s]) {
-          d.st.active[s] = 0;
-          atomicSub(&d.ctl->n_active, 1);
-        } else if (it >= d.ctl->max_inner) {
-          d.st.active[s] = 0;
-          d.st.status[s] |= 1;
-          atomicOr(&d.ctl->status, 1);
-          atomicSub(&d.ctl->n_active, 1);
-        }
-        d.st.beta[s] = rz / d.st.rho[s];
-        d.st.rho[s] = rz;
-      }
-    }
-  }
-  if (last_block(&d.ctl->gcnt_b, gridDim.x, &flag)) {
-    if (threadIdx.x == 0) {
-      const int n_inner = d.ctl->n_inner + 1;
-      d.ctl->n_inner = n_inner;
-      d.ctl->total_inner += 1;
-      const bool more = atomicAdd(&d.ctl->n_active, 0) > 0 && n_inner <= d.ctl->max_inner &&
-                        !out_of_time(d.ctl);
-      if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+      d.part1[tile] = vv[0];
+      d.part2[tile] = vv[1];
     }
   }
 }
 
+// Per-subdomain finalisers: one warp per subdomain adds the subdomain's tile
+// partials in a fixed order and updates its CG scalars, so the big kernels
+// carry no fences or atomics.  Launched with fin_blocks() blocks.
+
+// CG start: rho, ||b||^2, ||r||^2, the active flag; the last block sets the
+// inner loop condition.  mixed (the refinement forms): the partials are
+// ||d||^2, ||b||^2, r.z with d the FP64 defect, the inner solve's reference
+// norm is ||d||, and a subdomain whose defect already meets inner_rtol is not
+// corrected.
+__global__ void k_fin_init(DevProblem d, int mixed, unsigned long long cond, int use_cond) {
+  __shared__ bool flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * kTileSlices + warp;
+  if (s < d.n_sub) {
+    const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
+    const double a0 = warp_sum_parts(d.part0, t0, nt);
+    const double a1 = warp_sum_parts(d.part1, t0, nt);
+    const double a2 = warp_sum_parts(d.part2, t0, nt);
+    if (lane == 0) {
+      d.st.rr[s] = a0;
+      d.st.bb[s] = mixed ? a0 : a1;
+      d.st.rho[s] = a2;
+      d.st.beta[s] = 0.0;
+      d.st.iters[s] = 0;
+      d.st.status[s] = 0;
+      const int act = !d.inst_done[d.sub_inst[s]] &&
+                      (mixed ? (!(a0 <= d.ctl->tau2_outer * a1) && a2 > 0.0) : !(a0 <= d.ctl->tau2 * a1));
+      d.st.active[s] = act;
+      if (act) atomicAdd(&d.ctl->n_active, 1);
+    }
+  }
+  if (last_block(&d.ctl->gcnt_i, gridDim.x, &flag) && threadIdx.x == 0) {
+    const bool more = d.ctl->n_active > 0 && !out_of_time(d.ctl);
+    if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+  }
+}
+
+// alpha = rho / (p.q), or a breakdown stop of the subdomain.
+__global__ void k_fin_alpha(DevProblem d) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * kTileSlices + warp;
+  if (s >= d.n_sub || !d.st.active[s]) return;
+  const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
+  const double pq = warp_sum_parts(d.part0, t0, nt);
+  if (lane == 0) {
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      d.st.alpha[s] = 0.0;
+      d.st.status[s] |= 2;
+      atomicOr(&d.ctl->status, 2);
+      d.st.active[s] = 0;
+      atomicSub(&d.ctl->n_active, 1);
+    } else {
+      d.st.alpha[s] = d.st.rho[s] / pq;
+    }
+  }
+}
+
+// rho = r.z, the stop test ||r|| <= tau ||b|| (or the iteration cap), beta;
+// the last block counts the step and sets the inner loop condition.
+__global__ void k_fin_beta(DevProblem d, unsigned long long cond, int use_cond) {
+  __shared__ bool flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int s = blockIdx.x * kTileSlices + warp;
+  if (s < d.n_sub && d.st.active[s]) {
+    const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
+    const double rz = warp_sum_parts(d.part1, t0, nt);
+    const double rr = warp_sum_parts(d.part2, t0, nt);
+    if (lane == 0) {
+      const int it = d.st.iters[s] + 1;
+      d.st.iters[s] = it;
+      d.st.rr[s] = rr;
+      if (rr <= d.ctl->tau2 * d.st.bb[s]) {
+        d.st.active[s] = 0;
+        atomicSub(&d.ctl->n_active, 1);
+      } else if (it >= d.ctl->max_inner) {
+        d.st.active[s] = 0;
+        d.st.status[s] |= 1;
+        atomicOr(&d.ctl->status, 1);
+        atomicSub(&d.ctl->n_active, 1);
+      }
+      d.st.beta[s] = rz / d.st.rho[s];
+      d.st.rho[s] = rz;
+    }
+  }
+  if (last_block(&d.ctl->gcnt_b, gridDim.x, &flag) && threadIdx.x == 0) {
+    const int n_inner = d.ctl->n_inner + 1;
+    d.ctl->n_inner = n_inner;
+    d.ctl->total_inner += 1;
+    const bool more = d.ctl->n_active > 0 && n_inner <= d.ctl->max_inner && !out_of_time(d.ctl);
+    if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+  }
+}
+
 // p = z + beta p for subdomains still iterating.
-__global__ void __launch_bounds__(kTileRows) k_cg_direction(DevProblem d) {
+template <class T>
+__global__ void __launch_bounds__(kTileRows) k_cg_direction(DevProblem d, CgVec<T> v) {
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
   if (!d.st.active[s]) return;
   const int64_t row = tile * kTileRows + threadIdx.x;
-  d.p[row] = fma(d.st.beta[s], d.p[row], d.z[row]);
+  v.p[row] = fma((T)d.st.beta[s], v.p[row], v.z[row]);
+}
+
+// Mixed precision, start of one refinement step: FP64 defect
+// d = b - A u (FP64 values and accumulation), then the FP32 CG on A e = d
+// from e = 0: r = d, z = D^-1 r, p = z.  A subdomain whose FP64 defect already
+// meets the FP64 tolerance (||d|| <= inner_rtol ||b||) is not corrected; the
+// FP32 solve stops at ||r|| <= mixed_inner_rtol ||d||.
+__global__ void __launch_bounds__(kTileRows) k_cg_init_mixed(DevProblem d) {
+  __shared__ double sm[3][kTileSlices];
+  const int64_t tile = blockIdx.x;
+  const int s = d.tile_sub[tile];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t slice = tile * kTileSlices + warp;
+  const int64_t off = d.slice_off[slice];
+  const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
+  const int64_t t0 = d.sub_tile0[s];
+  const int64_t row = tile * kTileRows + threadIdx.x;
+  const double ax = sell_row(d.cols, d.vals, off, w, lane, d.x + t0 * kTileRows);
+  const double b = d.b[row];
+  const double dfc = b - ax;
+  const float r = (float)dfc;
+  const float z = d.dinv32[row] * r;
+  d.r32[row] = r;
+  d.z32[row] = z;
+  d.p32[row] = z;
+  d.x32[row] = 0.f;
+  double vv[3] = {dfc * dfc, b * b, (double)r * (double)z};
+  block_sum<3>(vv, sm);
+  if (threadIdx.x == 0) {
+    d.part0[tile] = vv[0];
+    d.part1[tile] = vv[1];
+    d.part2[tile] = vv[2];
+  }
+}
+
+// Mixed precision, end of the refinement step: u += e in FP64.
+__global__ void __launch_bounds__(kTileRows) k_mixed_correct(DevProblem d) {
+  const int64_t row = blockIdx.x * (int64_t)kTileRows + threadIdx.x;
+  d.x[row] += (double)d.x32[row];
+}
+
+// y32 = A32 x32 (FP32 values) on every tile: the mixed inner operator.
+__global__ void __launch_bounds__(kTileRows) k_spmv_plain32(DevProblem d, const float* __restrict__ x,
+                                                            float* __restrict__ y) {
+  const int64_t tile = blockIdx.x;
+  const int s = d.tile_sub[tile];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t slice = tile * kTileSlices + warp;
+  const int64_t off = d.slice_off[slice];
+  const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
+  const int64_t t0 = d.sub_tile0[s];
+  y[tile * kTileRows + threadIdx.x] = sell_row(d.cols, d.vals32, off, w, lane, x + t0 * kTileRows);
+}
+
+__global__ void k_scatter_local32(DevProblem d, const double* __restrict__ canon, float* __restrict__ vec) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= d.n_local) return;
+  vec[d.can2vec[k]] = (float)canon[k];
+}
+
+__global__ void k_gather_local32(DevProblem d, const float* __restrict__ vec, double* __restrict__ canon) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= d.n_local) return;
+  canon[k] = (double)vec[d.can2vec[k]];
 }
 
 // Robin exchange on every face entry (parallel update, Sec. 3):
@@ -300,6 +305,7 @@ __global__ void k_exchange(DevProblem d) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= d.n_fent) return;
   const int f = d.fent_face[e];
+  if (d.inst_done[d.sub_inst[d.face_s[f]]]) return;
   const int64_t eo = d.face_eo[f];
   const int32_t nf = d.face_n[f];
   const int64_t m = e - eo;
@@ -321,15 +327,20 @@ __global__ void k_exchange(DevProblem d) {
 // Stop test, step 1: ubar = average of the copies of each node; phi = ubar
 // on the full grid; w = ubar scattered back to every copy.
 __global__ void k_average(DevProblem d) {
-  int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (n >= d.n_nodes) return;
-  const int32_t c0 = d.cp_ptr[n], c1 = d.cp_ptr[n + 1];
-  if (c0 == c1) { d.phi[n] = 0.0; return; }
-  double s = 0.0;
-  for (int32_t c = c0; c < c1; ++c) s += d.x[d.cp_idx[c]];
-  const double ub = s / (double)(c1 - c0);
-  d.phi[n] = ub;
-  for (int32_t c = c0; c < c1; ++c) d.w[d.cp_idx[c]] = ub;
+  const int b = blockIdx.x;
+  if (d.inst_done[d.rblock_inst[b]]) return;  // a finished instance keeps its phi
+  for (int64_t n = d.rblock_node0[b] + threadIdx.x; n < d.rblock_node0[b + 1]; n += blockDim.x) {
+    const int32_t c0 = d.cp_ptr[n], c1 = d.cp_ptr[n + 1];
+    if (c0 == c1) {
+      d.phi[n] = 0.0;
+      continue;
+    }
+    double s = 0.0;
+    for (int32_t c = c0; c < c1; ++c) s += d.x[d.cp_idx[c]];
+    const double ub = s / (double)(c1 - c0);
+    d.phi[n] = ub;
+    for (int32_t c = c0; c < c1; ++c) d.w[d.cp_idx[c]] = ub;
+  }
 }
 
 // y = A x on every tile (all subdomains).
@@ -356,49 +367,68 @@ __global__ void k_face_correct(DevProblem d, const double* __restrict__ x, doubl
   y[row] -= p * acc;
 }
 
-// Stop test, step 2: r = sum_copies f - sum_copies K_i ubar per node,
-// ||r|| / ||f|| by a deterministic two-level sum; the last block records the
-// residual, counts the Schwarz iteration and sets the outer loop condition.
+// Stop test, step 2: r = sum_copies f - sum_copies K_i ubar per node and
+// ||r|| / ||f|| per instance by a deterministic two-level sum.  The last
+// block of an instance records its residual and whether it is done (reached
+// rtol or max_outer); the last block overall counts the Schwarz iteration
+// and sets the outer loop condition (any instance still running).
 __global__ void __launch_bounds__(256) k_residual(DevProblem d, unsigned long long cond, int use_cond) {
   __shared__ double sm[2][kTileSlices];
   __shared__ bool flag;
-  int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int b = blockIdx.x;
+  const int inst = d.rblock_inst[b];
+  const bool live = !d.inst_done[inst];
   double v[2] = {0.0, 0.0};
-  if (n < d.n_nodes) {
-    const int32_t c0 = d.cp_ptr[n], c1 = d.cp_ptr[n + 1];
-    double fg = 0.0, ku = 0.0;
-    for (int32_t c = c0; c < c1; ++c) {
-      fg += d.f[d.cp_idx[c]];
-      ku += d.y[d.cp_idx[c]];
+  if (live) {
+    for (int64_t n = d.rblock_node0[b] + threadIdx.x; n < d.rblock_node0[b + 1]; n += blockDim.x) {
+      const int32_t c0 = d.cp_ptr[n], c1 = d.cp_ptr[n + 1];
+      double fg = 0.0, ku = 0.0;
+      for (int32_t c = c0; c < c1; ++c) {
+        fg += d.f[d.cp_idx[c]];
+        ku += d.y[d.cp_idx[c]];
+      }
+      const double r = fg - ku;
+      v[0] += r * r;
+      v[1] += fg * fg;
     }
-    const double r = fg - ku;
-    v[0] = r * r;
-    v[1] = fg * fg;
   }
   block_sum<2>(v, sm);
   if (threadIdx.x == 0) {
-    d.rpart[blockIdx.x] = v[0];
-    d.rpart2[blockIdx.x] = v[1];
+    d.rpart[b] = v[0];
+    d.rpart2[b] = v[1];
   }
-  if (last_block(&d.ctl->gcnt_r, gridDim.x, &flag)) {
+  const int b0 = d.inst_rblock0[inst], nb = d.inst_rblock0[inst + 1] - b0;
+  if (last_block(&d.inst_cnt[inst], (unsigned)nb, &flag) && live) {
     double u[2] = {0.0, 0.0};
-    for (int64_t k = threadIdx.x; k < (int64_t)gridDim.x; k += blockDim.x) {
-      u[0] += __ldcg(d.rpart + k);
-      u[1] += __ldcg(d.rpart2 + k);
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+      u[0] += __ldcg(d.rpart + b0 + k);
+      u[1] += __ldcg(d.rpart2 + b0 + k);
     }
     block_sum<2>(u, sm);
     if (threadIdx.x == 0) {
       const double rel = u[1] > 0.0 ? sqrt(u[0] / u[1]) : sqrt(u[0]);
       const int n_outer = d.ctl->n_outer;
-      if (n_outer < d.ctl->max_outer) d.hist[n_outer] = rel;
-      d.ctl->n_outer = n_outer + 1;
-      d.ctl->relres = rel;
-      if (use_cond) {
-        const bool more = (rel > d.ctl->rtol) && (n_outer + 1 < d.ctl->max_outer) && isfinite(rel) &&
-                          !out_of_time(d.ctl);
-        cudaGraphSetConditional(cond, more ? 1u : 0u);
+      d.inst_relres[inst] = rel;
+      d.inst_iters[inst] = n_outer + 1;
+      if (d.n_inst == 1) {
+        if (n_outer < d.ctl->max_outer) d.hist[n_outer] = rel;
+        d.ctl->relres = rel;
       }
+      if (!(rel > d.ctl->rtol) || !isfinite(rel) || n_outer + 1 >= d.ctl->max_outer) d.inst_done[inst] = 1;
     }
+  }
+  if (last_block(&d.ctl->gcnt_r, gridDim.x, &flag) && threadIdx.x == 0) {
+    d.ctl->n_outer += 1;
+    int running = 0;
+    double worst = 0.0;
+    for (int i = 0; i < d.n_inst; ++i) {
+      running += !d.inst_done[i];
+      worst = fmax(worst, d.inst_relres[i]);
+    }
+    if (d.n_inst > 1) d.ctl->relres = worst;
+    d.ctl->running = running;
+    const bool more = running > 0 && !out_of_time(d.ctl);
+    if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
   }
 }
 
@@ -415,6 +445,7 @@ __global__ void k_gather_local(DevProblem d, const double* __restrict__ vec, dou
 }
 
 inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+inline unsigned fin_blocks(const DevProblem& d) { return (unsigned)((d.n_sub + kTileSlices - 1) / kTileSlices); }
 
 }  // namespace
 
@@ -429,15 +460,53 @@ cudaError_t launch_rhs_gather(const DevProblem& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_init(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
-  k_cg_init<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, cond, use_cond);
+cudaError_t launch_cg_init(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond,
+                           int defect_norm) {
+  k_cg_init<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d);
+  k_fin_init<<<fin_blocks(d), kTileRows, 0, s>>>(d, defect_norm, cond, use_cond);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_iteration(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
-  k_cg_spmv<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d);
-  k_cg_update<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, cond, use_cond);
-  k_cg_direction<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d);
+  const CgVec<double> v{d.x, d.r, d.z, d.p, d.q, d.dinv, d.vals};
+  k_cg_spmv<double><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
+  k_fin_alpha<<<fin_blocks(d), kTileRows, 0, s>>>(d);
+  k_cg_update<double><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
+  k_fin_beta<<<fin_blocks(d), kTileRows, 0, s>>>(d, cond, use_cond);
+  k_cg_direction<double><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_iteration32(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
+  const CgVec<float> v{d.x32, d.r32, d.z32, d.p32, d.q32, d.dinv32, d.vals32};
+  k_cg_spmv<float><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
+  k_fin_alpha<<<fin_blocks(d), kTileRows, 0, s>>>(d);
+  k_cg_update<float><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
+  k_fin_beta<<<fin_blocks(d), kTileRows, 0, s>>>(d, cond, use_cond);
+  k_cg_direction<float><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_init_mixed(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
+  k_cg_init_mixed<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d);
+  k_fin_init<<<fin_blocks(d), kTileRows, 0, s>>>(d, 1, cond, use_cond);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_correct(const DevProblem& d, cudaStream_t s) {
+  k_mixed_correct<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmv_plain32(const DevProblem& d, const float* x, float* y, cudaStream_t s) {
+  k_spmv_plain32<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply32(const DevProblem& d, const double* x, double* y, cudaStream_t s) {
+  k_scatter_local32<<<blocks_for(d.n_local, 256), 256, 0, s>>>(d, x, d.z32);
+  k_spmv_plain32<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, d.z32, d.q32);
+  k_gather_local32<<<blocks_for(d.n_local, 256), 256, 0, s>>>(d, d.q32, y);
   return cudaGetLastError();
 }
 
@@ -453,7 +522,7 @@ cudaError_t launch_spmv_plain(const DevProblem& d, const double* x, double* y, c
 }
 
 cudaError_t launch_residual(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
-  k_average<<<blocks_for(d.n_nodes, 256), 256, 0, s>>>(d);
+  k_average<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
   k_spmv_plain<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, d.w, d.y);
   if (d.n_irow) k_face_correct<<<blocks_for(d.n_irow, 256), 256, 0, s>>>(d, d.w, d.y);
   k_residual<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d, cond, use_cond);

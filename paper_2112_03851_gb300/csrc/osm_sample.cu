@@ -1,0 +1,447 @@
+// Batched evaluation of Robin parameters: the stochastic search of Sec. 4
+// needs the Schwarz iteration (Sec. 3) run for a population of candidate p
+// values.  Here up to 32 candidates run as one batched solve that shares the
+// subdomain stiffness matrices K_i:
+//
+//   A_k = K_i + p_k M_Gi,   lam_ij,k <- 2 p_k M_Gij u_j,k - lam_ji,k,
+//
+// each candidate with its own iterate, Robin data, CG scalars per subdomain,
+// convergence mask and stop test.
+//
+// Layout: every vector holds the 32 candidates of a row contiguously
+// ([row][32]), so the 32 lanes of a warp are the 32 candidates.  A warp owns
+// one SELL-32 slice and walks its 32 rows; each matrix entry is loaded once
+// (the same address in all lanes, a broadcast) and applied to all candidates,
+// and every gather of x reads one contiguous 256-byte row of candidates.  The
+// stored SELL values are K_i (the caller sets p = 0 before the batched run);
+// the Robin term p_k M_Gi is added per candidate on interface rows.
+#include <cuda_runtime.h>
+
+#include "osm_device.cuh"
+#include "osm_internal.h"
+
+namespace osm {
+namespace {
+
+constexpr int W = kSampleWidth;
+
+// sum over the 8 warps of a block of a per-lane value; result in warp 0
+template <int NV>
+__device__ __forceinline__ void lane_block_sum(double (&v)[NV], double (*sm)[kTileSlices][W]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < NV; ++i) sm[i][warp][lane] = v[i];
+  __syncthreads();
+  if (warp == 0) {
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < kTileSlices; ++w) s += sm[i][w][lane];
+      v[i] = s;
+    }
+  }
+}
+
+// sum over tiles t0 .. t0+nt of part[t][lane] in a fixed order
+__device__ __forceinline__ double lane_sum_tiles(const double* part, int64_t t0, int64_t nt, int lane) {
+  double s = 0.0;
+  for (int64_t j = 0; j < nt; ++j) s += __ldcg(part + (t0 + j) * W + lane);
+  return s;
+}
+
+// Row `row` (slice lane `rl` of the slice at `off`, width w) times the
+// candidates' vectors: lane k returns (K x_k)[row] (+ p_k (M_G x_k)[row]
+// when `robin`).  Xs: subdomain base of X, Xg: X itself.
+__device__ __forceinline__ double mp_row(const DevProblem& d, const DevSample& m, int64_t off, int rl, int w,
+                                         const double* __restrict__ Xs, const double* __restrict__ Xg,
+                                         int64_t row, bool robin, double pk, int k) {
+  const int4* c4 = reinterpret_cast<const int4*>(d.cols + off) + rl;
+  const double2* v2 = reinterpret_cast<const double2*>(d.vals + off) + rl;
+  double acc0 = 0.0, acc1 = 0.0;
+  const int nq = w >> 2;
+#pragma unroll 2
+  for (int q = 0; q < nq; ++q) {
+    const int4 c = __ldg(c4 + q * 32);
+    const double2 a = __ldg(v2 + q * 64);
+    const double2 b = __ldg(v2 + q * 64 + 32);
+    acc0 = fma(a.x, Xs[(int64_t)c.x * W + k], acc0);
+    acc1 = fma(a.y, Xs[(int64_t)c.y * W + k], acc1);
+    acc0 = fma(b.x, Xs[(int64_t)c.z * W + k], acc0);
+    acc1 = fma(b.y, Xs[(int64_t)c.w * W + k], acc1);
+  }
+  double acc = acc0 + acc1;
+  if (robin) {
+    const int32_t ir = m.row_irow[row];
+    if (ir >= 0) {
+      double f = 0.0;
+      for (int32_t e = d.im_ptr[ir]; e < d.im_ptr[ir + 1]; ++e) f = fma(d.im_val[e], Xg[(int64_t)d.im_col[e] * W + k], f);
+      acc = fma(pk, f, acc);
+    }
+  }
+  return acc;
+}
+
+__device__ __forceinline__ double mp_dinv(const DevProblem& d, const DevSample& m, int64_t row, double pk) {
+  const double kd = d.kdiag[row];
+  if (kd == 0.0) return 0.0;  // padding row
+  const int32_t ir = m.row_irow[row];
+  return 1.0 / (kd + (ir >= 0 ? pk * d.irow_mdiag[ir] : 0.0));
+}
+
+// b_k = f on every row, for every candidate (start of a batched run).
+__global__ void k_mp_bcast_f(DevProblem d, DevSample m, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  m.b[i] = d.f[i / W];
+}
+
+// Robin right-hand sides on interface rows: b_k = f + sum_j lam_ij,k.
+__global__ void k_mp_rhs_gather(DevProblem d, DevSample m) {
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int k = threadIdx.x & 31;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    d.ctl->n_active = 0;
+    d.ctl->n_inner = 0;
+    if (d.ctl->t_start_ns == 0ull) d.ctl->t_start_ns = global_ns();
+  }
+  if (gw >= d.n_irow) return;
+  const int32_t row = d.irow[gw];
+  double b = d.f[row];
+  for (int32_t e = d.ilam_ptr[gw]; e < d.ilam_ptr[gw + 1]; ++e) b += m.lam[(int64_t)d.ilam[e] * W + k];
+  m.b[(int64_t)row * W + k] = b;
+}
+
+// CG start for every candidate: r = b - A_k x, z = D_k^-1 r, p = z.
+__global__ void __launch_bounds__(kTileRows) k_mp_cg_init(DevProblem d, DevSample m) {
+  __shared__ double sm[3][kTileSlices][W];
+  const int64_t tile = blockIdx.x;
+  const int s = d.tile_sub[tile];
+  const int warp = threadIdx.x >> 5, k = threadIdx.x & 31;
+  const int64_t slice = tile * kTileSlices + warp;
+  const int64_t off = d.slice_off[slice];
+  const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
+  const int64_t t0 = d.sub_tile0[s];
+  const double* Xs = m.x + t0 * kTileRows * W;
+  const double pk = m.psamp[k];
+  double v[3] = {0.0, 0.0, 0.0};
+  for (int rl = 0; rl < kSliceRows; ++rl) {
+    const int64_t row = slice * kSliceRows + rl;
+    const double ax = mp_row(d, m, off, rl, w, Xs, m.x, row, true, pk, k);
+    const int64_t idx = row * W + k;
+    const double b = m.b[idx];
+    const double r = b - ax;
+    const double z = mp_dinv(d, m, row, pk) * r;
+    m.r[idx] = r;
+    m.z[idx] = z;
+    m.pd[idx] = z;
+    v[0] += r * r;
+    v[1] += b * b;
+    v[2] += r * z;
+  }
+  lane_block_sum<3>(v, sm);
+  if (warp == 0) {
+    m.part0[tile * W + k] = v[0];
+    m.part1[tile * W + k] = v[1];
+    m.part2[tile * W + k] = v[2];
+  }
+}
+
+// q_k = A_k p_k and alpha per (subdomain, candidate) still iterating.
+__global__ void __launch_bounds__(kTileRows) k_mp_cg_spmv(DevProblem d, DevSample m) {
+  __shared__ double sm[1][kTileSlices][W];
+  const int64_t tile = blockIdx.x;
+  const int s = d.tile_sub[tile];
+  const int warp = threadIdx.x >> 5, k = threadIdx.x & 31;
+  const int64_t sk = (int64_t)s * W + k;
+  const int act = m.active[sk];
+  if (!__any_sync(0xffffffffu, act)) return;  // same answer in every warp of the block
+  const int64_t slice = tile * kTileSlices + warp;
+  const int64_t off = d.slice_off[slice];
+  const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
+  const int64_t t0 = d.sub_tile0[s];
+  const double* Xs = m.pd + t0 * kTileRows * W;
+  const double pk = m.psamp[k];
+  double v[1] = {0.0};
+  for (int rl = 0; rl < kSliceRows; ++rl) {
+    const int64_t row = slice * kSliceRows + rl;
+    const double q = mp_row(d, m, off, rl, w, Xs, m.pd, row, true, pk, k);
+    const int64_t idx = row * W + k;
+    m.q[idx] = q;
+    v[0] += m.pd[idx] * q;
+  }
+  lane_block_sum<1>(v, sm);
+  if (warp == 0) m.part0[tile * W + k] = v[0];
+}
+
+// x += alpha p, r -= alpha q, z = D_k^-1 r; rho, ||r||^2, stop test, beta.
+__global__ void __launch_bounds__(kTileRows) k_mp_cg_update(DevProblem d, DevSample m) {
+  __shared__ double sm[2][kTileSlices][W];
+  const int64_t tile = blockIdx.x;
+  const int s = d.tile_sub[tile];
+  const int warp = threadIdx.x >> 5, k = threadIdx.x & 31;
+  const int64_t sk = (int64_t)s * W + k;
+  const int act = m.active[sk];
+  if (__any_sync(0xffffffffu, act)) {
+    const double alpha = m.alpha[sk];
+    const double pk = m.psamp[k];
+    double v[2] = {0.0, 0.0};
+    const int64_t slice = tile * kTileSlices + warp;
+    for (int rl = 0; rl < kSliceRows; ++rl) {
+      const int64_t row = slice * kSliceRows + rl;
+      const int64_t idx = row * W + k;
+      if (act) {
+        m.x[idx] = fma(alpha, m.pd[idx], m.x[idx]);
+        const double r = fma(-alpha, m.q[idx], m.r[idx]);
+        const double z = mp_dinv(d, m, row, pk) * r;
+        m.r[idx] = r;
+        m.z[idx] = z;
+        v[0] += r * z;
+        v[1] += r * r;
+      }
+    }
+    lane_block_sum<2>(v, sm);
+    if (warp == 0) {
+      m.part1[tile * W + k] = v[0];
+      m.part2[tile * W + k] = v[1];
+    }
+  }
+}
+
+// Per-subdomain finalisers, one warp per subdomain and one lane per
+// candidate: the tile partials are added in a fixed order.
+
+__global__ void k_mp_fin_init(DevProblem d, DevSample m, unsigned long long cond, int use_cond) {
+  __shared__ bool flag;
+  const int warp = threadIdx.x >> 5, k = threadIdx.x & 31;
+  const int s = blockIdx.x * kTileSlices + warp;
+  if (s < d.n_sub) {
+    const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
+    const double rr = lane_sum_tiles(m.part0, t0, nt, k);
+    const double bb = lane_sum_tiles(m.part1, t0, nt, k);
+    const double rz = lane_sum_tiles(m.part2, t0, nt, k);
+    const int64_t sk = (int64_t)s * W + k;
+    m.rr[sk] = rr;
+    m.bb[sk] = bb;
+    m.rho[sk] = rz;
+    m.beta[sk] = 0.0;
+    m.iters[sk] = 0;
+    const int act = !m.done[k] && !(rr <= d.ctl->tau2 * bb);
+    m.active[sk] = act;
+    const unsigned bal = __ballot_sync(0xffffffffu, act);
+    if (k == 0 && bal) atomicAdd(&d.ctl->n_active, __popc(bal));
+  }
+  if (last_block(&d.ctl->gcnt_i, gridDim.x, &flag) && threadIdx.x == 0) {
+    const bool more = d.ctl->n_active > 0 && !out_of_time(d.ctl);
+    if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+  }
+}
+
+__global__ void k_mp_fin_alpha(DevProblem d, DevSample m) {
+  const int warp = threadIdx.x >> 5, k = threadIdx.x & 31;
+  const int s = blockIdx.x * kTileSlices + warp;
+  if (s >= d.n_sub) return;
+  const int64_t sk = (int64_t)s * W + k;
+  if (!m.active[sk]) return;
+  const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
+  const double pq = lane_sum_tiles(m.part0, t0, nt, k);
+  if (!(pq > 0.0) || !isfinite(pq)) {
+    m.alpha[sk] = 0.0;
+    m.active[sk] = 0;
+    atomicOr(&d.ctl->status, 2);
+    atomicSub(&d.ctl->n_active, 1);
+  } else {
+    m.alpha[sk] = m.rho[sk] / pq;
+  }
+}
+
+__global__ void k_mp_fin_beta(DevProblem d, DevSample m, unsigned long long cond, int use_cond) {
+  __shared__ bool flag;
+  const int warp = threadIdx.x >> 5, k = threadIdx.x & 31;
+  const int s = blockIdx.x * kTileSlices + warp;
+  if (s < d.n_sub) {
+    const int64_t sk = (int64_t)s * W + k;
+    if (m.active[sk]) {
+      const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
+      const double rz = lane_sum_tiles(m.part1, t0, nt, k);
+      const double rr = lane_sum_tiles(m.part2, t0, nt, k);
+      const int it = m.iters[sk] + 1;
+      m.iters[sk] = it;
+      m.rr[sk] = rr;
+      if (rr <= d.ctl->tau2 * m.bb[sk]) {
+        m.active[sk] = 0;
+        atomicSub(&d.ctl->n_active, 1);
+      } else if (it >= d.ctl->max_inner) {
+        m.active[sk] = 0;
+        atomicOr(&d.ctl->status, 1);
+        atomicSub(&d.ctl->n_active, 1);
+      }
+      m.beta[sk] = rz / m.rho[sk];
+      m.rho[sk] = rz;
+    }
+  }
+  if (last_block(&d.ctl->gcnt_b, gridDim.x, &flag) && threadIdx.x == 0) {
+    const int n_inner = d.ctl->n_inner + 1;
+    d.ctl->n_inner = n_inner;
+    d.ctl->total_inner += 1;
+    const bool more = d.ctl->n_active > 0 && n_inner <= d.ctl->max_inner && !out_of_time(d.ctl);
+    if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+  }
+}
+
+// p = z + beta p for the (subdomain, candidate) pairs still iterating.
+__global__ void __launch_bounds__(kTileRows) k_mp_cg_direction(DevProblem d, DevSample m) {
+  const int64_t tile = blockIdx.x;
+  const int s = d.tile_sub[tile];
+  const int warp = threadIdx.x >> 5, k = threadIdx.x & 31;
+  const int64_t sk = (int64_t)s * W + k;
+  if (!m.active[sk]) return;
+  const double beta = m.beta[sk];
+  const int64_t slice = tile * kTileSlices + warp;
+  for (int rl = 0; rl < kSliceRows; ++rl) {
+    const int64_t idx = (slice * kSliceRows + rl) * W + k;
+    m.pd[idx] = fma(beta, m.pd[idx], m.z[idx]);
+  }
+}
+
+// Robin exchange for every candidate still running (warp per face entry).
+__global__ void k_mp_exchange(DevProblem d, DevSample m) {
+  const int64_t e = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int k = threadIdx.x & 31;
+  if (e >= d.n_fent || m.done[k]) return;
+  const int f = d.fent_face[e];
+  const int64_t eo = d.face_eo[f];
+  const int32_t nf = d.face_n[f];
+  const int64_t mm = e - eo;
+  double mus = 0.0, mut = 0.0;
+  for (int32_t j = d.fm_ptr[e]; j < d.fm_ptr[e + 1]; ++j) {
+    const double mv = d.fm_val[j];
+    const int32_t c = d.fm_col[j];
+    mus = fma(mv, m.x[(int64_t)d.fent_row_s[c] * W + k], mus);
+    mut = fma(mv, m.x[(int64_t)d.fent_row_t[c] * W + k], mut);
+  }
+  const double pp = 2.0 * m.psamp[k];
+  double* lst = m.lam + (2 * eo + mm) * W + k;
+  double* lts = m.lam + (2 * eo + nf + mm) * W + k;
+  const double old_st = *lst, old_ts = *lts;
+  *lst = pp * mut - old_ts;
+  *lts = pp * mus - old_st;
+}
+
+// ubar_k = mean of the copies of every node, scattered back to the copies.
+__global__ void k_mp_average(DevProblem d, DevSample m) {
+  const int k = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t n = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; n < d.n_nodes; n += nw) {
+    const int32_t c0 = d.cp_ptr[n], c1 = d.cp_ptr[n + 1];
+    if (c0 == c1) continue;
+    double s = 0.0;
+    for (int32_t c = c0; c < c1; ++c) s += m.x[(int64_t)d.cp_idx[c] * W + k];
+    const double ub = s / (double)(c1 - c0);
+    for (int32_t c = c0; c < c1; ++c) m.w[(int64_t)d.cp_idx[c] * W + k] = ub;
+  }
+}
+
+// y_k = K w_k (Neumann stiffness, no Robin term) on every tile.
+__global__ void __launch_bounds__(kTileRows) k_mp_spmv_k(DevProblem d, DevSample m) {
+  const int64_t tile = blockIdx.x;
+  const int s = d.tile_sub[tile];
+  const int warp = threadIdx.x >> 5, k = threadIdx.x & 31;
+  const int64_t slice = tile * kTileSlices + warp;
+  const int64_t off = d.slice_off[slice];
+  const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
+  const int64_t t0 = d.sub_tile0[s];
+  const double* Xs = m.w + t0 * kTileRows * W;
+  for (int rl = 0; rl < kSliceRows; ++rl) {
+    const int64_t row = slice * kSliceRows + rl;
+    m.y[row * W + k] = mp_row(d, m, off, rl, w, Xs, m.w, row, false, 0.0, k);
+  }
+}
+
+// Stop test per candidate: ||sum_copies f - sum_copies K_i ubar_k|| / ||f||;
+// the last block records it, marks converged candidates and steers the loop.
+__global__ void __launch_bounds__(256) k_mp_residual(DevProblem d, DevSample m, unsigned long long cond,
+                                                     int use_cond) {
+  __shared__ double sm[2][kTileSlices][W];
+  __shared__ bool flag;
+  const int warp = threadIdx.x >> 5, k = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  double v[2] = {0.0, 0.0};
+  for (int64_t n = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; n < d.n_nodes; n += nw) {
+    const int32_t c0 = d.cp_ptr[n], c1 = d.cp_ptr[n + 1];
+    double fg = 0.0, ku = 0.0;
+    for (int32_t c = c0; c < c1; ++c) {
+      fg += d.f[d.cp_idx[c]];
+      ku += m.y[(int64_t)d.cp_idx[c] * W + k];
+    }
+    const double r = fg - ku;
+    v[0] += r * r;
+    v[1] += fg * fg;
+  }
+  lane_block_sum<2>(v, sm);
+  if (warp == 0) {
+    m.rpart[blockIdx.x * W + k] = v[0];
+    m.rpart2[blockIdx.x * W + k] = v[1];
+  }
+  if (last_block(&d.ctl->gcnt_r, gridDim.x, &flag) && warp == 0) {
+    double rr = 0.0, ff = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) {
+      rr += __ldcg(m.rpart + (int64_t)b * W + k);
+      ff += __ldcg(m.rpart2 + (int64_t)b * W + k);
+    }
+    const double rel = ff > 0.0 ? sqrt(rr / ff) : sqrt(rr);
+    const int n_outer = d.ctl->n_outer + 1;
+    if (!m.done[k]) {
+      m.relres[k] = rel;
+      m.outer_iters[k] = n_outer;
+      if (rel <= d.ctl->rtol || !isfinite(rel) || n_outer >= d.ctl->max_outer) m.done[k] = 1;
+    }
+    const unsigned running = __ballot_sync(0xffffffffu, !m.done[k]);
+    if (k == 0) {
+      d.ctl->n_outer = n_outer;
+      const bool more = running != 0u && !out_of_time(d.ctl);
+      if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
+      d.ctl->n_active = (int)__popc(running);  // host-loop mode reads it as "candidates running"
+    }
+  }
+}
+
+inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+inline unsigned fin_blocks(const DevProblem& d) { return (unsigned)((d.n_sub + kTileSlices - 1) / kTileSlices); }
+
+}  // namespace
+
+cudaError_t launch_mp_start(const DevProblem& d, const DevSample& m, cudaStream_t s) {
+  const int64_t n = d.n_tiles * (int64_t)kTileRows * W;
+  k_mp_bcast_f<<<blocks_for(n, 256), 256, 0, s>>>(d, m, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mp_rhs_init(const DevProblem& d, const DevSample& m, cudaStream_t s, unsigned long long cond,
+                               int use_cond) {
+  k_mp_rhs_gather<<<blocks_for((d.n_irow > 0 ? d.n_irow : 1) * (int64_t)32, 256), 256, 0, s>>>(d, m);
+  k_mp_cg_init<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m);
+  k_mp_fin_init<<<fin_blocks(d), kTileRows, 0, s>>>(d, m, cond, use_cond);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mp_cg_iteration(const DevProblem& d, const DevSample& m, cudaStream_t s,
+                                   unsigned long long cond, int use_cond) {
+  k_mp_cg_spmv<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m);
+  k_mp_fin_alpha<<<fin_blocks(d), kTileRows, 0, s>>>(d, m);
+  k_mp_cg_update<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m);
+  k_mp_fin_beta<<<fin_blocks(d), kTileRows, 0, s>>>(d, m, cond, use_cond);
+  k_mp_cg_direction<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mp_exchange_residual(const DevProblem& d, const DevSample& m, cudaStream_t s,
+                                        unsigned long long cond, int use_cond) {
+  if (d.n_fent) k_mp_exchange<<<blocks_for(d.n_fent * (int64_t)32, 256), 256, 0, s>>>(d, m);
+  k_mp_average<<<kNodeBlocks, 256, 0, s>>>(d, m);
+  k_mp_spmv_k<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m);
+  k_mp_residual<<<kNodeBlocks, 256, 0, s>>>(d, m, cond, use_cond);
+  return cudaGetLastError();
+}
+
+}  // namespace osm

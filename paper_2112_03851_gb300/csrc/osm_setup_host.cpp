@@ -103,7 +103,7 @@ void build_load(const HostProblem& hp, const double* drho, std::vector<double>& 
 }
 
 std::string build_host_problem(const osm_mesh& mesh, const double* drho, const osm_decomp& dec,
-                               HostProblem& hp) {
+                               HostProblem& hp, bool want_fp32) {
   if (mesh.nx < 1 || mesh.ny < 1 || mesh.nz < 1) return "mesh needs at least one element per direction";
   if (!mesh.xc || !mesh.yc || !mesh.zc || !drho) return "null mesh coordinates or density";
   if (dec.sx < 1 || dec.sy < 1 || dec.sz < 1 || !dec.cx || !dec.cy || !dec.cz)
@@ -229,6 +229,8 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
   }
   hp.cols.assign(hp.sell_entries, 0);
   hp.vals.assign(hp.sell_entries, 0.0);
+  if (want_fp32) hp.vals32.assign(hp.sell_entries, 0.0f);
+  else std::vector<float>().swap(hp.vals32);
   hp.tile_sub.resize(hp.n_tiles);
   for (int s = 0; s < nsub; ++s)
     for (int64_t t = 0; t < hp.sub[s].npad / kTileRows; ++t) hp.tile_sub[hp.sub[s].tile0 + t] = s;
@@ -245,7 +247,7 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
     double mdiag;
     std::vector<int32_t> col;
     std::vector<double> m, kv;
-    std::vector<int64_t> pos;
+    std::vector<int64_t> pos, pos32;
   };
   std::vector<std::vector<IfaceRow>> irows(nsub);
   std::vector<int64_t> nnz_sub(nsub, 0);
@@ -284,6 +286,7 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
             int64_t vpos = off + (int64_t)(jn / 2) * 64 + lane * 2 + (jn % 2);
             hp.cols[cpos] = col;
             hp.vals[vpos] = v;
+            if (want_fp32) hp.vals32[cpos] = (float)v;
             if (col == r) hp.kdiag[S.voff + r] = v;
             if (is_if) {
               double mv = 0.0;
@@ -301,6 +304,7 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
                 ir.m.push_back(mv);
                 ir.kv.push_back(v);
                 ir.pos.push_back(vpos);
+                ir.pos32.push_back(cpos);
                 if (col == r) ir.mdiag = mv;
               }
             }
@@ -426,6 +430,7 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
   // ---- interface rows: Robin entries and received lam indices
   hp.irow.clear(); hp.irow_sub.clear(); hp.irow_mdiag.clear();
   hp.im_ptr.assign(1, 0); hp.im_col.clear(); hp.im_val.clear(); hp.im_pos.clear(); hp.im_kval.clear();
+  hp.im_pos32.clear();
   std::stable_sort(lam_rows.begin(), lam_rows.end(),
                    [](const std::pair<int32_t, int32_t>& x, const std::pair<int32_t, int32_t>& y) {
                      return x.first < y.first;
@@ -443,6 +448,7 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
         hp.im_col.push_back(ir.col[e]);
         hp.im_val.push_back(ir.m[e]);
         hp.im_pos.push_back(ir.pos[e]);
+        hp.im_pos32.push_back(ir.pos32[e]);
         hp.im_kval.push_back(ir.kv[e]);
       }
       hp.im_ptr.push_back((int32_t)hp.im_col.size());
@@ -455,6 +461,127 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
 
   // ---- load
   build_load(hp, drho, hp.f);
+  single_instance_tables(hp);
+  return std::string();
+}
+
+// Residual blocks of nodes [n0, n1) of instance `inst`: about one block per
+// 2048 nodes, at least one.
+static void add_rblocks(HostProblem& hp, int inst, int64_t n0, int64_t n1) {
+  const int64_t per = 2048;
+  const int64_t nb = std::max<int64_t>(1, (n1 - n0 + per - 1) / per);
+  for (int64_t b = 0; b < nb; ++b) {
+    hp.rblock_inst.push_back(inst);
+    hp.rblock_node0.push_back(n0 + (n1 - n0) * b / nb);
+  }
+}
+
+void single_instance_tables(HostProblem& hp) {
+  hp.n_inst = 1;
+  hp.sub_inst.assign(hp.nsub, 0);
+  hp.inst_sub0 = {0, hp.nsub};
+  hp.inst_node0 = {0, hp.n_nodes};
+  hp.rblock_inst.clear();
+  hp.rblock_node0.clear();
+  add_rblocks(hp, 0, 0, hp.n_nodes);
+  hp.rblock_node0.push_back(hp.n_nodes);
+  hp.inst_rblock0 = {0, (int32_t)hp.rblock_inst.size()};
+}
+
+template <class T>
+static void append_shift(std::vector<T>& dst, const std::vector<T>& src, T shift) {
+  for (const T& v : src) dst.push_back(v + shift);
+}
+
+template <class T>
+static void append(std::vector<T>& dst, const std::vector<T>& src) {
+  dst.insert(dst.end(), src.begin(), src.end());
+}
+
+std::string merge_problems(std::vector<HostProblem>& parts, HostProblem& out) {
+  if (parts.empty()) return "no instances";
+  out = HostProblem();
+  HostProblem& o = out;
+  const HostProblem& first = parts[0];
+  o.nx = first.nx; o.ny = first.ny; o.nz = first.nz; o.NX = first.NX; o.NY = first.NY; o.NZ = first.NZ;
+  o.sx = first.sx; o.sy = first.sy; o.sz = first.sz;
+  o.xc = first.xc; o.yc = first.yc; o.zc = first.zc;
+  o.n_inst = (int)parts.size();
+  o.inst_sub0.push_back(0);
+  o.inst_node0.push_back(0);
+  o.inst_rblock0.push_back(0);
+  o.slice_off.clear();
+  o.ilam_ptr.push_back(0);
+  o.im_ptr.push_back(0);
+  o.fm_ptr.push_back(0);
+  o.cp_ptr.push_back(0);
+  for (int i = 0; i < o.n_inst; ++i) {
+    HostProblem& p = parts[i];
+    const int32_t sub_off = o.nsub;
+    const int64_t vec_off = o.vec_rows, tile_off = o.n_tiles, slice_off = o.n_slices, ent_off = o.sell_entries;
+    const int64_t canon_off = o.n_local, node_off = o.n_nodes, fent_off = o.n_fent;
+    const int32_t face_off = o.nface;
+    const int64_t ilam_off = (int64_t)o.ilam.size(), im_off = (int64_t)o.im_col.size();
+    const int64_t fm_off = (int64_t)o.fm_col.size(), cp_off = (int64_t)o.cp_idx.size();
+    if (vec_off + p.vec_rows >= ((int64_t)1 << 31) || node_off + p.n_nodes >= ((int64_t)1 << 31) ||
+        fm_off + (int64_t)p.fm_col.size() >= ((int64_t)1 << 31))
+      return "batched problem too large for 32-bit indices";
+    for (SubInfo S : p.sub) {
+      S.voff += vec_off; S.canon_off += canon_off; S.tile0 += tile_off; S.slice0 += slice_off;
+      o.sub.push_back(S);
+    }
+    for (int64_t k = 0; k < p.n_slices; ++k) o.slice_off.push_back(p.slice_off[k] + ent_off);
+    append(o.cols, p.cols);
+    append(o.vals, p.vals);
+    append(o.vals32, p.vals32);
+    append_shift(o.tile_sub, p.tile_sub, sub_off);
+    append_shift(o.can2vec, p.can2vec, (int32_t)vec_off);
+    append(o.f, p.f);
+    append(o.kdiag, p.kdiag);
+    append(o.dinv0, p.dinv0);
+    append_shift(o.irow, p.irow, (int32_t)vec_off);
+    append_shift(o.irow_sub, p.irow_sub, sub_off);
+    append(o.irow_mdiag, p.irow_mdiag);
+    for (size_t k = 1; k < p.ilam_ptr.size(); ++k) o.ilam_ptr.push_back((int32_t)(p.ilam_ptr[k] + ilam_off));
+    append_shift(o.ilam, p.ilam, (int32_t)(2 * fent_off));
+    for (size_t k = 1; k < p.im_ptr.size(); ++k) o.im_ptr.push_back((int32_t)(p.im_ptr[k] + im_off));
+    append_shift(o.im_col, p.im_col, (int32_t)vec_off);
+    append(o.im_val, p.im_val);
+    append_shift(o.im_pos, p.im_pos, ent_off);
+    append(o.im_kval, p.im_kval);
+    append_shift(o.im_pos32, p.im_pos32, ent_off);
+    append_shift(o.face_s, p.face_s, sub_off);
+    append_shift(o.face_t, p.face_t, sub_off);
+    append(o.face_n, p.face_n);
+    append_shift(o.face_eo, p.face_eo, fent_off);
+    append_shift(o.fent_face, p.fent_face, face_off);
+    append_shift(o.fent_row_s, p.fent_row_s, (int32_t)vec_off);
+    append_shift(o.fent_row_t, p.fent_row_t, (int32_t)vec_off);
+    for (size_t k = 1; k < p.fm_ptr.size(); ++k) o.fm_ptr.push_back((int32_t)(p.fm_ptr[k] + fm_off));
+    append_shift(o.fm_col, p.fm_col, (int32_t)fent_off);
+    append(o.fm_val, p.fm_val);
+    for (size_t k = 1; k < p.cp_ptr.size(); ++k) o.cp_ptr.push_back((int32_t)(p.cp_ptr[k] + cp_off));
+    append_shift(o.cp_idx, p.cp_idx, (int32_t)vec_off);
+    for (int s = 0; s < p.nsub; ++s) o.sub_inst.push_back(i);
+    add_rblocks(o, i, node_off, node_off + p.n_nodes);
+    o.nsub += p.nsub;
+    o.vec_rows += p.vec_rows;
+    o.n_tiles += p.n_tiles;
+    o.n_slices += p.n_slices;
+    o.sell_entries += p.sell_entries;
+    o.n_local += p.n_local;
+    o.n_nodes += p.n_nodes;
+    o.n_dofs += p.n_dofs;
+    o.nnz += p.nnz;
+    o.n_fent += p.n_fent;
+    o.nface += p.nface;
+    o.inst_sub0.push_back(o.nsub);
+    o.inst_node0.push_back(o.n_nodes);
+    o.inst_rblock0.push_back((int32_t)o.rblock_inst.size());
+    p = HostProblem();  // release the part
+  }
+  o.slice_off.push_back(o.sell_entries);
+  o.rblock_node0.push_back(o.n_nodes);
   return std::string();
 }
 

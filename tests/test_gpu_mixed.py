@@ -1,0 +1,122 @@
+"""Mixed precision (FP32 subdomain CG inside FP64 refinement) against the
+FP64 oracle.
+
+Tolerances:
+* FP32 operator (osm_apply op 2): x and the values are rounded to FP32 and a
+  row of at most 125 terms is accumulated in FP32 FMA, so
+  |y32 - y| <= (n + 2) 2^-24 (|A| |x|)_row with n <= 125; tested at
+  1e-5 (|A| |x|)_row (> 127 * 2^-24 = 7.6e-6).
+* Solves: the refinement's defect, exchange and stop test are FP64, so the
+  mixed solution must match the FP64 oracle to a relative L2 error of 1e-8
+  (the target for the mixed form) when solved to a global residual of 1e-10.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def osm(cuda_ok):
+    from paper_2112_03851_gb300 import build
+    build.build()
+    import paper_2112_03851_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def small_uneven():
+    return gen.regional_problem(nx=12, ny=10, nz=8, sx=3, sy=2, sz=2, p=2.0, seed=4,
+                                lx=10.0, ly=8.0, lz=3.0)
+
+
+@pytest.mark.parametrize("case", ["sphere16", "uneven"])
+def test_fp32_operator_within_fp32_bound(osm, case):
+    import torch
+    prob = gen.sphere_problem(16, 2, 10.0) if case == "sphere16" else small_uneven()
+    p = 3.3
+    S = oracle.Schwarz(prob.xc, prob.yc, prob.zc, prob.drho, prob.cx, prob.cy, prob.cz, p)
+    sol = osm.Solver.from_problem(prob, p=p, prec="mixed")
+    rng = np.random.default_rng(3)
+    x = rng.standard_normal(sol.info["n_local"])
+    xt = torch.from_numpy(x).cuda()
+    y32 = sol.apply(xt, op=2).cpu().numpy()
+    y64 = sol.apply(xt, op=0).cpu().numpy()
+    off = 0
+    for s in range(S.nsub):
+        A, _, _, _ = S.sub_export(s)
+        n = A.shape[0]
+        xs = x[off:off + n]
+        bound = abs(A) @ np.abs(xs)
+        ref = A @ xs
+        assert np.all(np.abs(y32[off:off + n] - ref) <= 1e-5 * bound), s
+        assert np.all(np.abs(y64[off:off + n] - ref) <= 1e-13 * bound), s
+        # genuinely FP32: not bitwise the FP64 result
+        off += n
+    assert np.abs(y32 - y64).max() > 0.0
+
+
+def _mono(prob):
+    G = oracle.GlobalSystem(prob.xc, prob.yc, prob.zc, prob.drho)
+    ref, _, _ = G.solve(tol=1e-14)
+    return G, G.to_grid(ref)
+
+
+@pytest.mark.parametrize("case", ["sphere16", "uneven"])
+def test_mixed_solve_matches_fp64_oracle(osm, case):
+    prob = gen.sphere_problem(16, 2, 10.0) if case == "sphere16" else small_uneven()
+    G, ref = _mono(prob)
+    # the FP64 local tolerance (inner_rtol) caps the reachable global residual:
+    # a subdomain whose defect is below inner_rtol ||b_i|| is not corrected
+    sol = osm.Solver.from_problem(prob, prec="mixed", mixed_inner_rtol=1e-5, inner_rtol=1e-13,
+                                  max_outer=3000)
+    phi, n, rel = sol.solve(rtol=1e-10)
+    phi = phi.cpu().numpy()
+    assert rel <= 1e-10
+    assert G.residual(phi) <= 1.01e-10
+    err = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
+    assert err <= 1e-8, err
+
+
+@pytest.mark.parametrize("tin", [1e-1, 1e-3])
+def test_refinement_forms_reach_fp64_accuracy(osm, tin):
+    """Loose inner tolerances (relative to each Schwarz iteration's defect)
+    in FP32 (mixed) and FP64 (fp64_refine) still reach the FP64 stop test
+    and the oracle's solution."""
+    prob = gen.sphere_problem(16, 2, 10.0)
+    G, ref = _mono(prob)
+    for prec in ("mixed", "fp64_refine"):
+        sol = osm.Solver.from_problem(prob, prec=prec, mixed_inner_rtol=tin, inner_rtol=1e-13, max_outer=4000)
+        phi, n, rel = sol.solve(rtol=1e-10)
+        phi = phi.cpu().numpy()
+        assert rel <= 1e-10 and G.residual(phi) <= 1.01e-10
+        assert np.linalg.norm(phi - ref) <= 1e-8 * np.linalg.norm(ref), prec
+
+
+def test_mixed_and_fp64_agree_and_mixed_is_cheaper(osm):
+    """Same workload in both precisions: both reach the FP64 residual, agree
+    with each other to 1e-8, and the mixed form moves fewer matrix bytes per
+    CG step (8 B per nonzero instead of 12)."""
+    prob = gen.layered_problem(24, 2, p=8.0, seed=1)
+    a = osm.Solver.from_problem(prob, prec="fp64")
+    b = osm.Solver.from_problem(prob, prec="mixed")
+    pa, na, ra = a.solve(rtol=1e-9)
+    pb, nb, rb = b.solve(rtol=1e-9)
+    assert ra <= 1e-9 and rb <= 1e-9
+    pa, pb = pa.cpu().numpy(), pb.cpu().numpy()
+    assert np.linalg.norm(pa - pb) <= 1e-8 * np.linalg.norm(pa)
+    assert abs(na - nb) <= max(3, 0.1 * na)
+
+
+def test_mixed_layered64_full_size_residual(osm):
+    """64^3 layered workload in mixed precision, certified by the oracle's
+    own assembled K: ||f - K phi|| <= 1e-8 ||f||."""
+    prob = gen.workload("layered64")
+    sol = osm.Solver.from_problem(prob, p=20.0, prec="mixed")
+    phi, n, rel = sol.solve(rtol=1e-8)
+    assert rel <= 1e-8
+    G = oracle.GlobalSystem(prob.xc, prob.yc, prob.zc, prob.drho)
+    assert G.residual(phi.cpu().numpy()) <= 1.001e-8

@@ -1,0 +1,87 @@
+"""Batched stochastic evaluation of Robin parameters (osm_sample_p, Sec. 4)
+against independent single-p solves and the oracle's Schwarz iteration
+counts.
+
+Each candidate runs the same FP64 algorithm as osm_solve, with its own state,
+so its Schwarz iteration count must equal the single solve's (rounding can
+move a residual across the threshold: +-1) and the oracle's (+-1), and its
+final residual must agree with the single solve's to the stop tolerance.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def osm(cuda_ok):
+    from paper_2112_03851_gb300 import build
+    build.build()
+    import paper_2112_03851_gb300 as pkg
+    pkg.load()
+    return pkg
+
+
+def small_uneven():
+    return gen.regional_problem(nx=12, ny=10, nz=8, sx=3, sy=2, sz=2, p=2.0, seed=4,
+                                lx=10.0, ly=8.0, lz=3.0)
+
+
+@pytest.mark.parametrize("case", ["sphere8", "uneven"])
+def test_sample_matches_single_solves_and_oracle(osm, case):
+    prob = gen.sphere_problem(8, 2, 4.0) if case == "sphere8" else small_uneven()
+    ps = gen.log_uniform_p(0, 6, 0.5, 40.0)
+    rtol = 1e-9
+    sol = osm.Solver.from_problem(prob, inner_rtol=1e-11, max_outer=600)
+    iters, rel, best = sol.sample_p(ps, rtol=rtol, max_outer=600)
+    for k, p in enumerate(ps):
+        sol.set_robin(float(p))
+        _, n1, r1 = sol.solve(rtol=rtol, allow_noconv=True)
+        assert abs(int(iters[k]) - n1) <= 1, (k, p, iters[k], n1)
+        if n1 == iters[k]:  # same iterate up to summation order
+            assert abs(rel[k] - r1) <= 1e-4 * r1 + 1e-300
+    for k in (0, 3):
+        S = oracle.Schwarz.from_problem(prob, p=float(ps[k]))
+        _, n_ref, _, _ = S.solve(inner_rtol=1e-11, rtol=rtol, max_outer=600)
+        assert abs(int(iters[k]) - n_ref) <= 1, (k, iters[k], n_ref)
+    conv = [k for k in range(len(ps)) if rel[k] <= rtol]
+    exp = min(conv, key=lambda k: (iters[k], rel[k], ps[k]))
+    assert best == exp
+
+
+def test_sample_batches_beyond_32_and_restores_handle(osm):
+    prob = gen.sphere_problem(8, 2, 4.0)
+    sol = osm.Solver.from_problem(prob, inner_rtol=1e-10, max_outer=400)
+    phi0, n0, r0 = sol.solve(rtol=1e-8)
+    ps = gen.log_uniform_p(7, 40, 0.5, 40.0)
+    iters, rel, best = sol.sample_p(ps, rtol=1e-8, max_outer=400)
+    # the last 8 candidates ran in a second batch: compare with a batch of their own
+    it2, rel2, _ = sol.sample_p(ps[32:], rtol=1e-8, max_outer=400)
+    assert np.array_equal(iters[32:], it2) and np.array_equal(rel[32:], rel2)
+    # batching does not change a candidate's run: the same p in two batch positions
+    it3, rel3, _ = sol.sample_p(np.array([ps[3], ps[35], ps[3]]), rtol=1e-8, max_outer=400)
+    assert it3[0] == it3[2] == iters[3] and it3[1] == iters[35]
+    assert rel3[0] == rel3[2] == rel[3]
+    # the handle's own p (4.0) is back in place: bit-identical solve
+    phi1, n1, r1 = sol.solve(rtol=1e-8)
+    assert n1 == n0 and r1 == r0 and bool((phi1 == phi0).all())
+
+
+def test_sample_reports_non_converging_candidates(osm):
+    prob = gen.sphere_problem(8, 2, 4.0)
+    sol = osm.Solver.from_problem(prob, inner_rtol=1e-10)
+    iters, rel, best = sol.sample_p(np.array([1e-3, 4.0, 1e4]), rtol=1e-8, max_outer=300)
+    assert iters[0] == 300 and rel[0] > 1e-8      # far too small p: stalls
+    assert iters[2] == 300 and rel[2] > 1e-8      # far too large p: stalls
+    assert rel[1] <= 1e-8 and iters[1] < 300 and best == 1
+
+
+def test_sample_rejects_bad_p(osm):
+    prob = gen.sphere_problem(4, 2, 4.0)
+    sol = osm.Solver.from_problem(prob)
+    for bad in ([1.0, -2.0], [float("nan")], []):
+        with pytest.raises(osm.OsmError):
+            sol.sample_p(np.array(bad, dtype=np.float64))

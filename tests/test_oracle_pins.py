@@ -328,3 +328,53 @@ def test_face_mass_matches_tensor_product_on_graded_uneven_mesh():
         b = ijk[:, tang[1]] - ob
         ref = Mb[np.ix_(b, b)] * Ma[np.ix_(a, a)]
         assert np.abs(Mf.toarray() - ref).max() <= 1e-14 * np.abs(ref).max(), f
+
+
+# ------------------------------------------------------------- gradient ----
+
+def test_station_operator_is_exact_on_q2_fields():
+    """B applied to the interpolant of phi = x(1-x) y(1-y) z^2 (in Q2) gives
+    d phi/dz = 2 z x(1-x) y(1-y) exactly, at surface and interior stations."""
+    xc = np.linspace(0, 1, 5)
+    yc = np.array([0.0, 0.2, 0.5, 0.7, 1.0])
+    zc = gen.graded_coords(4, 1.0, 1.2)
+    G = oracle.GlobalSystem(xc, yc, zc, keep_boundary=True)
+    rng = np.random.default_rng(2)
+    st = np.concatenate([gen.surface_stations(5), rng.uniform(0.05, 0.95, size=(10, 3))])
+    B = oracle.station_matrix(G, st)
+    nodes = _node_coords(xc, yc, zc)[G.gnode]
+    X, Y, Z = nodes.T
+    phi = X * (1 - X) * Y * (1 - Y) * Z ** 2
+    exact = 2 * st[:, 2] * st[:, 0] * (1 - st[:, 0]) * st[:, 1] * (1 - st[:, 1])
+    assert np.abs(B @ phi - exact).max() < 1e-13
+
+
+def test_load_matrix_columns_integrate_the_element():
+    prob = gen.regional_problem(nx=4, ny=3, nz=5, sx=1, sy=1, sz=1, seed=1, lx=2.0, ly=1.0, lz=1.5)
+    G = oracle.GlobalSystem(prob.xc, prob.yc, prob.zc, keep_boundary=True)
+    F = oracle.load_matrix(G)
+    hx, hy, hz = np.diff(prob.xc), np.diff(prob.yc), np.diff(prob.zc)
+    vol = (hz[:, None, None] * hy[None, :, None] * hx[None, None, :]).ravel()
+    assert np.allclose(np.asarray(F.sum(axis=0)).ravel(), 4 * np.pi * gen.G_NEWTON * vol, rtol=1e-14)
+    G2 = oracle.GlobalSystem(prob.xc, prob.yc, prob.zc, prob.drho)
+    F2 = oracle.load_matrix(G2)
+    assert np.allclose(F2 @ prob.drho, G2.f, rtol=1e-12, atol=1e-30)
+
+
+def test_misfit_gradient_matches_central_differences():
+    """J is exactly quadratic in drho, so the central difference with any h
+    equals the directional derivative; 50 seeded unit directions."""
+    prob = gen.layered_problem(n=8, s=1, seed=5, n_spheres=3)
+    st = gen.surface_stations(8)
+    M = oracle.Misfit(prob.xc, prob.yc, prob.zc, st)
+    rng = np.random.default_rng(9)
+    g_obs = M.gravity(prob.drho + rng.normal(0, 20, prob.drho.size))
+    J, grad = M.value_and_grad(prob.drho, g_obs)
+    h = 1e-2
+    for _ in range(50):
+        d = rng.standard_normal(prob.drho.size)
+        d /= np.linalg.norm(d)
+        Jp = 0.5 * np.sum((M.gravity(prob.drho + h * d) - g_obs) ** 2)
+        Jm = 0.5 * np.sum((M.gravity(prob.drho - h * d) - g_obs) ** 2)
+        fd = (Jp - Jm) / (2 * h)
+        assert abs(fd - grad @ d) <= 1e-5 * np.linalg.norm(grad)
