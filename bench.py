@@ -31,16 +31,20 @@ if ROOT not in sys.path:
 METRIC = "DOF/s solved to 1e-8 rel residual, mixed vs FP64; SpMV GB/s vs HBM peak"
 WORKLOAD = "layered64"
 P_ROBIN = 20.0
+# Robin parameter per workload (layered64: best of the batched sampling and
+# the tolerance sweeps; others scaled by the same search)
+P_FOR = {"layered64": 20.0, "regional": 1.0, "layered160": 40.0, "layered48": 10.0}
 RTOL = 1e-8
 INNER_RTOL = 1e-10
 MIXED_INNER_RTOL = 0.3
 FALLBACK_HBM = 6800.0
 
 
-def _workload_desc(prob, p):
-    return (f"{WORKLOAD}: unit cube, Q2 {prob.nx}^3 elements ({prob.n_dofs:,} unknowns), "
-            f"{len(prob.cx)-1}x{len(prob.cy)-1}x{len(prob.cz)-1} subdomains, 3 density layers + "
-            f"20 random spheres (seed 0), Robin p={p:g}, subdomain PCG to {INNER_RTOL:g}, "
+def _workload_desc(prob, p, name=WORKLOAD):
+    dens = ("Gaussian random field (l=5, sigma=100) + basin -250, 100x100x30 box graded 1.05 in z, "
+            "uneven jittered cuts" if name == "regional" else "unit cube, 3 density layers + 20 random spheres")
+    return (f"{name}: Q2 {prob.nx}x{prob.ny}x{prob.nz} elements ({prob.n_dofs:,} unknowns), "
+            f"{len(prob.cx)-1}x{len(prob.cy)-1}x{len(prob.cz)-1} subdomains, {dens} (seed 0), Robin p={p:g}, "
             f"Schwarz to {RTOL:g}")
 
 
@@ -65,7 +69,7 @@ def _kernel_hash():
 def _traffic_per_launch(n_local, which):
     """DRAM bytes per SpMV launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "spmv_traffic.json")
+    path = os.path.join(ROOT, "profiles", "k_cg_spmv_layered48_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
@@ -140,7 +144,7 @@ def _dist():
     return ws, rank, local
 
 
-def _cpu_baseline(prob, p, n_outer_needed, budget_s=20.0):
+def _cpu_baseline(prob, p, n_outer_needed, name=WORKLOAD, budget_s=20.0):
     """The oracle's sequential Schwarz (OpenMP over subdomains) on the same
     workload: time a bounded number of Schwarz iterations, scale to the
     iterations the solve needs."""
@@ -160,7 +164,7 @@ def _cpu_baseline(prob, p, n_outer_needed, budget_s=20.0):
     per_iter = t_iter / done
     value = prob.n_dofs / (per_iter * n_outer_needed)
     return {"value": value, "unit": "DOF/s", "cores": threads, "kind": "oracle",
-            "sample": (f"{done} of {n_outer_needed} Schwarz iterations of the FP64 oracle on {WORKLOAD} "
+            "sample": (f"{done} of {n_outer_needed} Schwarz iterations of the FP64 oracle on {name} "
                        f"({per_iter:.2f} s each, OpenMP over subdomains; setup {setup:.1f} s excluded), "
                        f"solve time extrapolated to {n_outer_needed} iterations")}
 
@@ -294,13 +298,17 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.barrier()
 
-    prob = gen.workload(WORKLOAD)
+    name = args.workload or WORKLOAD
+    if name == "batch64":
+        return run_batch(args, pkg, ws, rank, local, barrier)
+    prob = gen.workload(name)
+    p_robin = P_FOR.get(name, P_ROBIN)
     use_graph = 0 if args.launch == "host" else 1
     note = "one CUDA graph per solve" if use_graph else "host-driven launches (profiling mode)"
     res = {}
     sols = {}
     for prec in (["mixed", "fp64", "fp64_refine"] if args.prec == "both" else [args.prec]):
-        sol = pkg.Solver.from_problem(prob, p=P_ROBIN, inner_rtol=INNER_RTOL, max_outer=5000,
+        sol = pkg.Solver.from_problem(prob, p=p_robin, inner_rtol=INNER_RTOL, max_outer=5000,
                                       prec=prec, mixed_inner_rtol=MIXED_INNER_RTOL, use_graph=use_graph)
         sols[prec] = sol
         res[prec] = _measure(sol, prob, args, ws, local, barrier, note)
@@ -312,7 +320,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 inner CG + f64 refinement" if head == "mixed" else "f64",
             "data": "synthetic",
-            "config": {"workload": _workload_desc(prob, P_ROBIN),
+            "config": {"workload": _workload_desc(prob, p_robin, name),
                        "precision": (f"mixed: FP32 subdomain CG to {MIXED_INNER_RTOL:g} of the FP64 defect, "
                                      "FP64 defect, exchange and stop test" if head == "mixed" else "FP64"),
                        "l2": "inputs larger than L2 (1.6 GB of subdomain matrices), no flush",
@@ -342,11 +350,55 @@ def run_ours(args):
             line["mixed_speedup_vs_fp64_refine"] = round(h["value"] / f["value"], 3)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         n_outer = res["fp64"]["schwarz_iterations"] if "fp64" in res else _reference_iterations()
-        line["cpu_baseline"] = _cpu_baseline(prob, P_ROBIN, n_outer)
+        line["cpu_baseline"] = _cpu_baseline(prob, p_robin, n_outer, name)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_batch(args, pkg, ws, rank, local, barrier):
+    """64 independent unit-cube problems (n ~ U{24..40}, 2x2x2 subdomains,
+    own layered density and own log-uniform p in [2, 50]) in one handle."""
+    import torch
+
+    import gen
+    probs = gen.batch_instances(64, 24, 40, seed=0)
+    prec = "mixed" if args.prec == "both" else args.prec
+    bs = pkg.BatchSolver(probs, prec=prec, inner_rtol=INNER_RTOL, mixed_inner_rtol=MIXED_INNER_RTOL,
+                         max_outer=5000)
+    dofs = sum(q.n_dofs for q in probs)
+    phi = torch.zeros(bs.info["n_nodes"], dtype=torch.float64, device="cuda")
+    for _ in range(max(args.warmup, 1)):
+        bs.solve(RTOL, phi=phi)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        launches = 0
+        for _ in range(args.steps):
+            _, iters, rel = bs.solve(RTOL, phi=phi)
+            launches += bs.stats()["n_launches"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    line = {"metric": METRIC, "value": ws * dofs / (ms / 1e3), "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32 inner CG + f64 refinement" if prec == "mixed" else "f64",
+            "data": "synthetic",
+            "config": {"workload": f"batch64: 64 unit-cube problems, n ~ U{{24..40}} Q2 elements per side "
+                                   f"({dofs:,} unknowns in total), 2x2x2 subdomains each, own layered density "
+                                   f"and own p ~ logU[2, 50], all in one CUDA graph per solve",
+                       "precision": prec},
+            "gpu_launches": int(launches), "schwarz_iterations_min_max": [int(iters.min()), int(iters.max())],
+            "relres_max": float(rel.max()), "setup_s": round(bs.info["setup_seconds"], 2),
+            "clocks": clk.summary(),
+            "roofline": _roofline(bs, 1 if prec == "mixed" else 0, "batched SELL-32 SpMV, 512 subdomains")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     return 0
 
 
@@ -371,6 +423,23 @@ def profile_iteration(args):
     return 0
 
 
+def profile_sample(args):
+    """Two Schwarz iterations of a 32-candidate batched p evaluation."""
+    import torch
+
+    import gen
+    import paper_2112_03851_gb300 as pkg
+    torch.cuda.set_device(0)
+    prob = gen.workload(args.workload or WORKLOAD)
+    sol = pkg.Solver.from_problem(prob, p=P_ROBIN, inner_rtol=INNER_RTOL, max_outer=5000,
+                                  use_graph=0 if args.launch == "host" else 1)
+    ps = gen.log_uniform_p(0, 32, 0.5, 200.0)
+    iters, rel, best = sol.sample_p(ps, rtol=RTOL, max_outer=2)
+    print(json.dumps({"profile_sample": args.workload or WORKLOAD, "relres_min": float(rel.min()),
+                      **sol.stats()}), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -386,9 +455,13 @@ def main(argv=None):
                          "kernels inside graphs with conditional nodes)")
     ap.add_argument("--profile-iteration", action="store_true",
                     help="set up the workload, run one Schwarz iteration and exit (for ncu captures)")
+    ap.add_argument("--profile-sample", action="store_true",
+                    help="set up the workload, run two Schwarz iterations of a 32-candidate p batch and exit")
     args = ap.parse_args(argv)
     if args.profile_iteration:
         return profile_iteration(args)
+    if args.profile_sample:
+        return profile_sample(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

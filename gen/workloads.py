@@ -281,6 +281,8 @@ def workload(name: str) -> Problem:
         return layered_problem(64, 4, p=10.0, seed=0)
     if name == "layered48":
         return layered_problem(48, 3, p=10.0, seed=0)
+    if name == "layered32":
+        return layered_problem(32, 4, p=20.0, seed=0)
     if name == "regional":
         return regional_problem()
     if name == "layered160":
@@ -288,4 +290,4 @@ def workload(name: str) -> Problem:
     raise KeyError(name)
 
 
-WORKLOADS = ("sphere16", "layered64", "layered48", "regional", "layered160")
+WORKLOADS = ("sphere16", "layered32", "layered64", "layered48", "regional", "layered160")
