@@ -64,6 +64,7 @@ def lib():
             "orc_basis_1d": (None, [d, vp, vp]),
             "orc_element": (None, [d, d, d, vp, vp, vp]),
             "orc_face_element": (None, [d, d, vp]),
+            "orc_face_stiffness": (None, [d, d, vp]),
             "orc_gauss_points": (None, [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp]),
             "orc_global_create": (vp, [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, C.c_int]),
             "orc_global_n": (i64, [vp]),
@@ -75,6 +76,9 @@ def lib():
             "orc_pcg": (C.c_int, [i64, vp, vp, vp, vp, vp, d, C.c_int, vp]),
             "orc_sz_create": (vp, [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, C.c_int,
                                    C.c_int, vp, vp, vp, vp]),
+            "orc_sz_create_tc": (vp, [C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, C.c_int, C.c_int,
+                                      C.c_int, vp, vp, vp, vp]),
+            "orc_sz_face_stiffness_export": (None, [vp, C.c_int, vp]),
             "orc_sz_nsub": (C.c_int, [vp]),
             "orc_sz_nface": (C.c_int, [vp]),
             "orc_sz_global_n": (i64, [vp]),
@@ -135,6 +139,13 @@ def face_element(ha: float, hb: float):
     M = np.zeros((9, 9))
     lib().orc_face_element(ha, hb, _ptr(M))
     return M
+
+
+def face_stiffness(ha: float, hb: float):
+    """Tangential Q2 stiffness S[9,9] of an ha x hb face element."""
+    S = np.zeros((9, 9))
+    lib().orc_face_stiffness(ha, hb, _ptr(S))
+    return S
 
 
 def gauss_points(xc, yc, zc):
@@ -246,22 +257,32 @@ def _np64(a):
 # -------------------------------------------------------------- Schwarz ----
 
 class Schwarz:
-    """Sequential optimized Schwarz iteration (Sec. 3, oo0 Robin condition).
+    """Sequential optimized Schwarz iteration (Sec. 3).
 
-    ``p`` is a scalar or one value per subdomain (subdomain s = a + sx(b + sy c)).
+    ``p`` is a scalar or one value per subdomain (subdomain s = a + sx(b + sy c)):
+    the zeroth-order Robin condition.  ``tc = (p_lo, q_lo, p_hi, q_hi)``
+    instead selects the second-order / unsymmetric condition on every face:
+    operator p + q(-d^2/dtau^2), (p_lo, q_lo) on the lower side of the face,
+    (p_hi, q_hi) on the upper side.
     """
 
-    def __init__(self, xc, yc, zc, drho, cx, cy, cz, p):
+    def __init__(self, xc, yc, zc, drho, cx, cy, cz, p=None, tc=None):
         self.xc, self.yc, self.zc = _f64(xc), _f64(yc), _f64(zc)
         self.cx, self.cy, self.cz = _i32(cx), _i32(cy), _i32(cz)
         sx, sy, sz = len(cx) - 1, len(cy) - 1, len(cz) - 1
-        p_sub = _f64(np.broadcast_to(np.asarray(p, dtype=np.float64), (sx * sy * sz,)))
         self.drho = _f64(drho)
-        self.p_sub = p_sub
         L = lib()
-        h = L.orc_sz_create(len(xc) - 1, len(yc) - 1, len(zc) - 1, _ptr(self.xc), _ptr(self.yc),
-                            _ptr(self.zc), _ptr(self.drho), sx, sy, sz, _ptr(self.cx), _ptr(self.cy),
-                            _ptr(self.cz), _ptr(p_sub))
+        args = (len(xc) - 1, len(yc) - 1, len(zc) - 1, _ptr(self.xc), _ptr(self.yc),
+                _ptr(self.zc), _ptr(self.drho), sx, sy, sz, _ptr(self.cx), _ptr(self.cy), _ptr(self.cz))
+        if tc is not None:
+            self.tc = _f64(tc)
+            assert self.tc.shape == (4,)
+            self.p_sub = None
+            h = L.orc_sz_create_tc(*args, _ptr(self.tc))
+        else:
+            self.tc = None
+            self.p_sub = _f64(np.broadcast_to(np.asarray(p, dtype=np.float64), (sx * sy * sz,)))
+            h = L.orc_sz_create(*args, _ptr(self.p_sub))
         if not h:
             raise RuntimeError("oracle decomposition failed")
         self._h = h
@@ -270,7 +291,9 @@ class Schwarz:
         self.n_nodes = (2 * len(xc) - 1) * (2 * len(yc) - 1) * (2 * len(zc) - 1)
 
     @classmethod
-    def from_problem(cls, prob, p=None):
+    def from_problem(cls, prob, p=None, tc=None):
+        if tc is not None:
+            return cls(prob.xc, prob.yc, prob.zc, prob.drho, prob.cx, prob.cy, prob.cz, tc=tc)
         return cls(prob.xc, prob.yc, prob.zc, prob.drho, prob.cx, prob.cy, prob.cz,
                    prob.p if p is None else p)
 
@@ -317,6 +340,14 @@ class Schwarz:
         m = np.zeros(rp[-1])
         lib().orc_sz_face_export(self._h, f, _ptr(g), _ptr(rp), _ptr(ci), _ptr(m))
         return g, sp.csr_matrix((m, ci, rp), shape=(n, n))
+
+    def face_stiffness_export(self, f):
+        """Tangential stiffness of face f, same node order as face_export."""
+        import scipy.sparse as sp
+        g, Mf = self.face_export(f)
+        sv = np.zeros(Mf.nnz)
+        lib().orc_sz_face_stiffness_export(self._h, f, _ptr(sv))
+        return sp.csr_matrix((sv, Mf.indices, Mf.indptr), shape=Mf.shape)
 
     def get_lambda(self, f, side):
         out = np.zeros(self.face_info(f)[3])

@@ -20,6 +20,14 @@
  *        (K_i + p_i M_Gi) u_i = f_i + sum_j lam_ij
  *        lam_ij <- (p_i + p_j) M_Gij u_j - lam_ji
  *     where lam_ij is the weak Robin datum on face G_ij received by i from j.
+ *     Second-order ("oo2") and unsymmetric conditions (Sec. 3, Table 1):
+ *     the operator of subdomain s on a face is p_s + q_s (-d^2/dtau^2)
+ *     (Fourier symbol p_s + q_s k^2), whose weak form is p_s M + q_s S with
+ *     S the face's tangential Q2 stiffness; then
+ *        (K_i + sum_faces (p_i M_Gij + q_i S_Gij)) u_i = f_i + sum_j lam_ij
+ *        lam_ij <- (p_i + p_j) M_Gij u_j + (q_i + q_j) S_Gij u_j - lam_ji.
+ *     In the unsymmetric form the lower side of every face (smaller
+ *     coordinate along its normal) takes (p1, q1), the upper side (p2, q2).
  *   - Sec. 6 stop test: global relative residual ||f - K ubar|| / ||f||
  *     with ubar the average of the subdomain copies at interface nodes.
  *
@@ -110,6 +118,29 @@ void orc_face_element(double ha, double hb, double *M)
         for (int I = 0; I < 9; ++I)
             for (int J = 0; J < 9; ++J)
                 M[I * 9 + J] += W * fa[I % 3] * fb[I / 3] * fa[J % 3] * fb[J / 3];
+    }
+}
+
+/* 2-D Q2 tangential stiffness S[9*9] of an ha x hb rectangle, local node
+ * a + 3b: S_IJ = int grad_t(phi_I) . grad_t(phi_J) over the face (the weak
+ * form of -d^2/dtau^2 in the second-order transmission operator, Sec. 3). */
+void orc_face_stiffness(double ha, double hb, double *S)
+{
+    double pt[3], wt[3];
+    gauss3(pt, wt);
+    memset(S, 0, sizeof(double) * 81);
+    for (int qb = 0; qb < 3; ++qb)
+    for (int qa = 0; qa < 3; ++qa) {
+        double W = wt[qa] * wt[qb] * ha * hb;
+        double fa[3], da[3], fb[3], db[3];
+        orc_basis_1d(pt[qa], fa, da);
+        orc_basis_1d(pt[qb], fb, db);
+        for (int I = 0; I < 9; ++I)
+            for (int J = 0; J < 9; ++J) {
+                double ga_i = da[I % 3] / ha * fb[I / 3], gb_i = fa[I % 3] * db[I / 3] / hb;
+                double ga_j = da[J % 3] / ha * fb[J / 3], gb_j = fa[J % 3] * db[J / 3] / hb;
+                S[I * 9 + J] += W * (ga_i * ga_j + gb_i * gb_j);
+            }
     }
 }
 
@@ -495,6 +526,8 @@ typedef struct {
     int64_t n;              /* face unknowns */
     int32_t *loc_s, *loc_t; /* local unknown index on each side */
     int64_t *rp; int32_t *ci; double *m;   /* face mass, face-node CSR */
+    double *sv;                /* face tangential stiffness, same CSR */
+    double ps, qs, pt, qt;     /* transmission coefficients of side s and side t */
     double *lam_st, *lam_ts;   /* Robin data received by s (from t) and by t (from s) */
 } orc_face;
 
@@ -567,6 +600,7 @@ static void face_build(orc_sz *Z, orc_face *F, int s, int t, int axis, int plane
     }
     F->ci = malloc(sizeof(int32_t) * (F->rp[n] ? F->rp[n] : 1));
     F->m = calloc(F->rp[n] ? F->rp[n] : 1, sizeof(double));
+    F->sv = calloc(F->rp[n] ? F->rp[n] : 1, sizeof(double));
     r = 0;
     for (int b = b0; b <= b1; ++b)
     for (int a = a0; a <= a1; ++a) {
@@ -583,8 +617,9 @@ static void face_build(orc_sz *Z, orc_face *F, int s, int t, int axis, int plane
     const double *cb = axis == 2 ? g->yc : g->zc;
     for (int eb = b0 / 2; eb < b1 / 2; ++eb)
     for (int ea = a0 / 2; ea < a1 / 2; ++ea) {
-        double Mf[81];
+        double Mf[81], Sf[81];
         orc_face_element(ca[ea + 1] - ca[ea], cb[eb + 1] - cb[eb], Mf);
+        orc_face_stiffness(ca[ea + 1] - ca[ea], cb[eb + 1] - cb[eb], Sf);
         int32_t loc[9];
         for (int I = 0; I < 9; ++I) {
             int a = 2 * ea + I % 3, b = 2 * eb + I / 3;
@@ -598,41 +633,52 @@ static void face_build(orc_sz *Z, orc_face *F, int s, int t, int axis, int plane
                 for (int64_t k = F->rp[loc[I]]; k < F->rp[loc[I] + 1]; ++k)
                     if (F->ci[k] == loc[J]) pos = k;
                 F->m[pos] += Mf[I * 9 + J];
+                F->sv[pos] += Sf[I * 9 + J];
             }
         }
     }
     free(fmap);
 }
 
-/* Add p * M_face into the local matrix of side `which` (0 = s, 1 = t). */
+/* Add the weak transmission operator p M_face + q S_face of side `which`
+ * (0 = s, 1 = t) into that side's local matrix. */
 static void face_add_robin(orc_sz *Z, const orc_face *F, int which)
 {
     orc_sub *U = &Z->sub[which ? F->t : F->s];
     const int32_t *loc = which ? F->loc_t : F->loc_s;
+    const double p = which ? F->pt : F->ps, q = which ? F->qt : F->qs;
     for (int64_t r = 0; r < F->n; ++r)
         for (int64_t k = F->rp[r]; k < F->rp[r + 1]; ++k) {
             int64_t pos = find_col(&U->S, loc[r], loc[F->ci[k]]);
-            U->S.v[pos] += U->p * F->m[k];
+            U->S.v[pos] += p * F->m[k] + q * F->sv[k];
         }
 }
 
-/* face mass apply: y = M_face x|face */
-static void face_apply(const orc_face *F, const double *u, const int32_t *loc, double *y)
+/* face apply: y = M_face x|face and ys = S_face x|face */
+static void face_apply(const orc_face *F, const double *u, const int32_t *loc, double *y, double *ys)
 {
     for (int64_t r = 0; r < F->n; ++r) {
-        double acc = 0.0;
-        for (int64_t k = F->rp[r]; k < F->rp[r + 1]; ++k) acc += F->m[k] * u[loc[F->ci[k]]];
+        double acc = 0.0, accs = 0.0;
+        for (int64_t k = F->rp[r]; k < F->rp[r + 1]; ++k) {
+            acc += F->m[k] * u[loc[F->ci[k]]];
+            accs += F->sv[k] * u[loc[F->ci[k]]];
+        }
         y[r] = acc;
+        ys[r] = accs;
     }
 }
 
 /*
  * Build the decomposition.  cx/cy/cz are element-index cuts (s+1 entries,
- * first 0, last n).  p_sub[s] is the Robin parameter used by subdomain s.
+ * first 0, last n).  Transmission coefficients: with tc == NULL subdomain s
+ * uses the Robin parameter p_sub[s] on all its faces (q = 0); otherwise every
+ * face uses tc = {p_lo, q_lo, p_hi, q_hi}: (p_lo, q_lo) in the condition of
+ * the subdomain on the lower side of the face (smaller coordinate along the
+ * normal), (p_hi, q_hi) in that of the upper side.
  */
-orc_sz *orc_sz_create(int nx, int ny, int nz, const double *xc, const double *yc, const double *zc,
-                      const double *drho, int sx, int sy, int sz, const int32_t *cx,
-                      const int32_t *cy, const int32_t *cz, const double *p_sub)
+static orc_sz *sz_create(int nx, int ny, int nz, const double *xc, const double *yc, const double *zc,
+                         const double *drho, int sx, int sy, int sz, const int32_t *cx,
+                         const int32_t *cy, const int32_t *cz, const double *p_sub, const double *tc)
 {
     orc_sz *Z = calloc(1, sizeof(orc_sz));
     geom_init(&Z->g, nx, ny, nz, xc, yc, zc);
@@ -647,7 +693,7 @@ orc_sz *orc_sz_create(int nx, int ny, int nz, const double *xc, const double *yc
         orc_sub *U = &Z->sub[s];
         U->ex0 = cx[a]; U->ex1 = cx[a + 1]; U->ey0 = cy[b]; U->ey1 = cy[b + 1];
         U->ez0 = cz[c]; U->ez1 = cz[c + 1];
-        U->p = p_sub[s];
+        U->p = p_sub ? p_sub[s] : 0.0;
         if (build_box(&Z->g, &lc, U->ex0, U->ex1, U->ey0, U->ey1, U->ez0, U->ez1, 0, &U->S)) bad |= 1;
         int64_t n = U->S.n ? U->S.n : 1;
         U->f = calloc(n, sizeof(double)); U->b = calloc(n, sizeof(double)); U->u = calloc(n, sizeof(double));
@@ -672,7 +718,13 @@ orc_sz *orc_sz_create(int nx, int ny, int nz, const double *xc, const double *yc
         face_build(Z, &Z->face[nf++], s, t, 2, 2 * cz[c + 1], 2 * cx[a], 2 * cx[a + 1], 2 * cy[b], 2 * cy[b + 1]);
     }
     Z->nface = nf;
-    for (int f = 0; f < nf; ++f) { face_add_robin(Z, &Z->face[f], 0); face_add_robin(Z, &Z->face[f], 1); }
+    for (int f = 0; f < nf; ++f) {
+        orc_face *F = &Z->face[f];
+        if (tc) { F->ps = tc[0]; F->qs = tc[1]; F->pt = tc[2]; F->qt = tc[3]; }
+        else { F->ps = Z->sub[F->s].p; F->qs = 0.0; F->pt = Z->sub[F->t].p; F->qt = 0.0; }
+        face_add_robin(Z, F, 0);
+        face_add_robin(Z, F, 1);
+    }
     /* global system for the stop test */
     if (build_box(&Z->g, &cache, 0, nx, 0, ny, 0, nz, 0, &Z->KG)) { cache_free(&cache); return NULL; }
     Z->fG = calloc(Z->KG.n ? Z->KG.n : 1, sizeof(double));
@@ -689,6 +741,20 @@ orc_sz *orc_sz_create(int nx, int ny, int nz, const double *xc, const double *yc
     for (int s = 0; s < Z->nsub; ++s)
         for (int64_t r = 0; r < Z->sub[s].S.n; ++r) Z->ncopy[Z->gunk[Z->sub[s].S.gnode[r]]]++;
     return Z;
+}
+
+orc_sz *orc_sz_create(int nx, int ny, int nz, const double *xc, const double *yc, const double *zc,
+                      const double *drho, int sx, int sy, int sz, const int32_t *cx,
+                      const int32_t *cy, const int32_t *cz, const double *p_sub)
+{
+    return sz_create(nx, ny, nz, xc, yc, zc, drho, sx, sy, sz, cx, cy, cz, p_sub, NULL);
+}
+
+orc_sz *orc_sz_create_tc(int nx, int ny, int nz, const double *xc, const double *yc, const double *zc,
+                         const double *drho, int sx, int sy, int sz, const int32_t *cx,
+                         const int32_t *cy, const int32_t *cz, const double *tc)
+{
+    return sz_create(nx, ny, nz, xc, yc, zc, drho, sx, sy, sz, cx, cy, cz, NULL, tc);
 }
 
 int orc_sz_nsub(const orc_sz *Z) { return Z->nsub; }
@@ -726,6 +792,13 @@ void orc_sz_face_export(const orc_sz *Z, int f, int32_t *gnode, int64_t *rp, int
     if (m) memcpy(m, F->m, sizeof(double) * F->rp[F->n]);
 }
 
+/* Face tangential stiffness values (same CSR as the face mass). */
+void orc_sz_face_stiffness_export(const orc_sz *Z, int f, double *sv)
+{
+    const orc_face *F = &Z->face[f];
+    memcpy(sv, F->sv, sizeof(double) * F->rp[F->n]);
+}
+
 /* Local system export: A_s = K_s + p_s M_Gs (CSR), f_s, node ids. */
 void orc_sz_sub_export(const orc_sz *Z, int s, int64_t *rp, int32_t *ci, double *v, double *f,
                        int32_t *gnode, double *u)
@@ -754,7 +827,11 @@ void orc_sz_set_global_rhs(orc_sz *Z, const double *fG)
 /*
  * One Schwarz iteration: b_s = f_s + sum lam; local Jacobi PCG from the
  * previous u_s to tol (relative to ||b_s||); then the parallel exchange
- * lam_st <- (p_s + p_t) M u_t - lam_ts,  lam_ts <- (p_s + p_t) M u_s - lam_st.
+ *   lam_st <- (p_s + p_t) M u_t + (q_s + q_t) S u_t - lam_ts,
+ *   lam_ts <- (p_s + p_t) M u_s + (q_s + q_t) S u_s - lam_st
+ * (the weak normal flux of the neighbour, -lam + (p M + q S) u, plus the
+ * receiving side's own transmission operator applied to the neighbour's
+ * trace).
  * Local PCG iteration counts are written to iters_sub (may be NULL).
  */
 void orc_sz_iterate(orc_sz *Z, double tol, int maxit, int32_t *iters_sub)
@@ -779,18 +856,19 @@ void orc_sz_iterate(orc_sz *Z, double tol, int maxit, int32_t *iters_sub)
     if (iters_sub) for (int s = 0; s < Z->nsub; ++s) iters_sub[s] = Z->sub[s].last_iters;
     for (int f = 0; f < Z->nface; ++f) {
         orc_face *F = &Z->face[f];
-        double *mu_t = malloc(sizeof(double) * (F->n ? F->n : 1));
-        double *mu_s = malloc(sizeof(double) * (F->n ? F->n : 1));
-        face_apply(F, Z->sub[F->t].u, F->loc_t, mu_t);
-        face_apply(F, Z->sub[F->s].u, F->loc_s, mu_s);
-        double pp = Z->sub[F->s].p + Z->sub[F->t].p;
+        int64_t nb = F->n ? F->n : 1;
+        double *mu_t = malloc(sizeof(double) * nb), *su_t = malloc(sizeof(double) * nb);
+        double *mu_s = malloc(sizeof(double) * nb), *su_s = malloc(sizeof(double) * nb);
+        face_apply(F, Z->sub[F->t].u, F->loc_t, mu_t, su_t);
+        face_apply(F, Z->sub[F->s].u, F->loc_s, mu_s, su_s);
+        double pp = F->ps + F->pt, qq = F->qs + F->qt;
         for (int64_t r = 0; r < F->n; ++r) {
-            double new_st = pp * mu_t[r] - F->lam_ts[r];
-            double new_ts = pp * mu_s[r] - F->lam_st[r];
+            double new_st = pp * mu_t[r] + qq * su_t[r] - F->lam_ts[r];
+            double new_ts = pp * mu_s[r] + qq * su_s[r] - F->lam_st[r];
             F->lam_st[r] = new_st;
             F->lam_ts[r] = new_ts;
         }
-        free(mu_t); free(mu_s);
+        free(mu_t); free(su_t); free(mu_s); free(su_s);
     }
 }
 
@@ -848,7 +926,8 @@ void orc_sz_destroy(orc_sz *Z)
     }
     for (int f = 0; f < Z->nface; ++f) {
         orc_face *F = &Z->face[f];
-        free(F->loc_s); free(F->loc_t); free(F->rp); free(F->ci); free(F->m); free(F->lam_st); free(F->lam_ts);
+        free(F->loc_s); free(F->loc_t); free(F->rp); free(F->ci); free(F->m); free(F->sv);
+        free(F->lam_st); free(F->lam_ts);
     }
     free(Z->sub); free(Z->face);
     box_free(&Z->KG); free(Z->fG); free(Z->gunk); free(Z->ubar); free(Z->work); free(Z->ncopy);
