@@ -40,12 +40,47 @@ MIXED_INNER_RTOL = 0.3
 FALLBACK_HBM = 6800.0
 
 
-def _workload_desc(prob, p, name=WORKLOAD):
-    dens = ("Gaussian random field (l=5, sigma=100) + basin -250, 100x100x30 box graded 1.05 in z, "
-            "uneven jittered cuts" if name == "regional" else "unit cube, 3 density layers + 20 random spheres")
+def _is_slab(name):
+    return name.startswith("slab")
+
+
+def _rtol_for(name):
+    # Table 2 runs the slab partitions to a residual of 1e-6
+    return 1e-6 if _is_slab(name) else RTOL
+
+
+def _tc_for(prob, name):
+    """Transmission coefficients of a workload: the slab partitions use the
+    unsymmetric second-order condition optimised by CMA-ES on the Fourier
+    rate over the interface's frequency band (Sec. 4-6): from the lowest
+    Dirichlet mode of the 250 x 15 face to pi over the tangential node
+    spacing.  Others: None (zeroth-order Robin, P_FOR)."""
+    if not _is_slab(name):
+        return None
+    import math
+
+    from paper_2112_03851_gb300 import search
+    ly, lz = prob.yc[-1] - prob.yc[0], prob.zc[-1] - prob.zc[0]
+    h = min(float((prob.yc[1:] - prob.yc[:-1]).min()), float((prob.zc[1:] - prob.zc[:-1]).min()))
+    kmin, kmax = math.pi * math.hypot(1.0 / ly, 1.0 / lz), math.pi / (0.5 * h)
+    c, rho, _ = search.optimise_fourier("oo2_unsym", kmin, kmax, seed=0, max_iter=2000)
+    return tuple(float(v) for v in c), float(rho), (kmin, kmax)
+
+
+def _workload_desc(prob, p, name=WORKLOAD, tc=None):
+    if name == "regional":
+        dens = ("Gaussian random field (l=5, sigma=100) + basin -250, 100x100x30 box graded 1.05 in z, "
+                "uneven jittered cuts")
+    elif _is_slab(name):
+        dens = ("250x250x15 box, slabs along x (Sec. 6 partition), layered crust + buried crater "
+                "(breccia lens -250, central uplift +200, peak ring +100) + N(0,10^2) noise")
+    else:
+        dens = "unit cube, 3 density layers + 20 random spheres"
+    cond = (f"oo2 unsymmetric (p_lo, q_lo, p_hi, q_hi) = ({', '.join(f'{v:.4g}' for v in tc[0])}), "
+            f"Fourier rho_max {tc[1]:.4f} on k in [{tc[2][0]:.4g}, {tc[2][1]:.4g}]" if tc else f"Robin p={p:g}")
     return (f"{name}: Q2 {prob.nx}x{prob.ny}x{prob.nz} elements ({prob.n_dofs:,} unknowns), "
-            f"{len(prob.cx)-1}x{len(prob.cy)-1}x{len(prob.cz)-1} subdomains, {dens} (seed 0), Robin p={p:g}, "
-            f"Schwarz to {RTOL:g}")
+            f"{len(prob.cx)-1}x{len(prob.cy)-1}x{len(prob.cz)-1} subdomains, {dens} (seed 0), {cond}, "
+            f"Schwarz to {_rtol_for(name):g}")
 
 
 def _peaks():
@@ -60,16 +95,16 @@ def _peaks():
 
 def _kernel_hash():
     h = hashlib.sha256()
-    for name in ("osm_kernels.cu", "osm_internal.h"):
+    for name in ("osm_kernels.cu", "osm_internal.h", "osm_device.cuh"):
         with open(os.path.join(ROOT, "paper_2112_03851_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def _traffic_per_launch(n_local, which):
-    """DRAM bytes per SpMV launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "k_cg_spmv_layered48_traffic.json")
+    """DRAM bytes per launch of kernel `which` from the committed ncu summary,
+    if it was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "cg_spmv_layered48_traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
@@ -135,6 +170,23 @@ class ClockSampler:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def aggregate_over_ranks(ms_local, units_local, device=None):
+    """Whole-job throughput of independent replicas: every rank processed
+    units_local in ms_local; the job takes the slowest rank's time (all-reduce
+    MAX) and processed the sum of the units (all-reduce SUM).  Returns
+    (value per second, slowest ms).  Works on any torch.distributed backend
+    (NCCL on the GPUs, gloo in the CPU tests); single process without one."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return units_local / (ms_local / 1e3), ms_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / (float(t.item()) / 1e3), float(t.item())
 
 
 def _dist():
@@ -210,7 +262,7 @@ def _reference_iterations():
         return 150
 
 
-def _measure(sol, prob, args, ws, local, barrier, use_graph_note):
+def _measure(sol, prob, args, ws, local, barrier, use_graph_note, rtol=RTOL):
     """Warm-up, the timed region (CUDA events, clocks sampled) and the
     end-to-end run through the public API from host buffers."""
     import numpy as np
@@ -218,7 +270,7 @@ def _measure(sol, prob, args, ws, local, barrier, use_graph_note):
     stream = torch.cuda.current_stream()
     phi = torch.zeros(sol.info["n_nodes"], dtype=torch.float64, device="cuda")
     for _ in range(max(args.warmup, 1)):
-        sol.solve(RTOL, phi=phi)
+        sol.solve(rtol, phi=phi)
     st = sol.stats()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches = 0
@@ -228,16 +280,13 @@ def _measure(sol, prob, args, ws, local, barrier, use_graph_note):
         torch.cuda.synchronize()
         ev0.record(stream)
         for _ in range(args.steps):
-            _, it, rel = sol.solve(RTOL, phi=phi)
+            _, it, rel = sol.solve(rtol, phi=phi)
             launches += sol.stats()["n_launches"]
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
+    value, ms_max = aggregate_over_ranks(ms, prob.n_dofs, device="cuda")
     # end to end: new density from a host array in, solution out to pinned
     # host memory, every step
     phi_host = torch.empty(sol.info["n_nodes"], dtype=torch.float64, pin_memory=True)
@@ -247,34 +296,36 @@ def _measure(sol, prob, args, ws, local, barrier, use_graph_note):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         sol.set_density(drho)
-        sol.solve(RTOL, phi=phi)
+        sol.solve(rtol, phi=phi)
         phi_host.copy_(phi, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / args.steps
-    te = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+    e2e_value, _ = aggregate_over_ranks(e2e_s * 1e3, prob.n_dofs, device="cuda")
     return {
-        "value": ws * prob.n_dofs / (ms_max / 1e3), "ms_per_step": ms_max, "relres": rel,
+        "value": value, "ms_per_step": ms_max, "relres": rel,
         "schwarz_iterations": st["n_outer"], "cg_steps_per_solve": st["n_cg_steps"],
         "launches_per_step": int(st["n_launches"]), "gpu_launches": int(launches),
         "clocks": clk.summary(), "launch_mode": use_graph_note,
-        "e2e": {"value": ws * prob.n_dofs / float(te.item()), "unit": "DOF/s",
+        "e2e": {"value": e2e_value, "unit": "DOF/s",
                 "h2d_bytes_per_step": 2 * sol.info["vec_rows"] * 8,   # load vector f and b
                 "d2h_bytes_per_step": sol.info["n_nodes"] * 8},       # phi
+        "_phi": phi,
     }
 
 
 def _roofline(sol, prec, name):
+    """Roofline of the CG-step SpMV kernel (prec 2: k_cg_spmv_dir32, 3:
+    k_cg_spmv<double>), timed alone with every subdomain active."""
     ms = sol.profile_spmv(20, prec=prec)
     nbytes = sol.spmv_bytes(prec)
     peak, kind = _peaks()
     achieved = nbytes / (ms / 1e3) / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4),
-            "traffic": _traffic_per_launch(sol.info["n_local"], "fp32" if prec else "fp64"),
-            "kernel": name, "peak_kind": f"{kind} hbm_gbs (copy)", "ms_per_launch": round(ms, 5),
-            "algorithmic_bytes": nbytes}
+            "traffic": _traffic_per_launch(sol.info["n_local"], "k_cg_spmv_dir32" if prec == 2 else "k_cg_spmv_double"),
+            "kernel": name, "peak_kind": f"{kind} hbm_gbs (copy), burst (kernel timed alone)",
+            "ms_per_launch": round(ms, 5), "algorithmic_bytes": nbytes,
+            "col_bytes": sol.info["col_bytes_fp64" if prec in (0, 3) else "col_bytes_fp32"]}
 
 
 def run_ours(args):
@@ -301,17 +352,24 @@ def run_ours(args):
     name = args.workload or WORKLOAD
     if name == "batch64":
         return run_batch(args, pkg, ws, rank, local, barrier)
+    if name == "sample32":
+        return run_sample(args, pkg, ws, rank, local, barrier)
+    if name == "grad48":
+        return run_grad(args, pkg, ws, rank, local, barrier)
     prob = gen.workload(name)
     p_robin = P_FOR.get(name, P_ROBIN)
+    tc = _tc_for(prob, name)
+    rtol = _rtol_for(name)
     use_graph = 0 if args.launch == "host" else 1
     note = "one CUDA graph per solve" if use_graph else "host-driven launches (profiling mode)"
     res = {}
     sols = {}
     for prec in (["mixed", "fp64", "fp64_refine"] if args.prec == "both" else [args.prec]):
-        sol = pkg.Solver.from_problem(prob, p=p_robin, inner_rtol=INNER_RTOL, max_outer=5000,
-                                      prec=prec, mixed_inner_rtol=MIXED_INNER_RTOL, use_graph=use_graph)
+        sol = pkg.Solver.from_problem(prob, p=p_robin, tc=tc[0] if tc else None, inner_rtol=INNER_RTOL,
+                                      max_outer=5000, prec=prec, mixed_inner_rtol=MIXED_INNER_RTOL,
+                                      use_graph=use_graph)
         sols[prec] = sol
-        res[prec] = _measure(sol, prob, args, ws, local, barrier, note)
+        res[prec] = _measure(sol, prob, args, ws, local, barrier, note, rtol)
         res[prec]["setup_s"] = round(sol.info["setup_seconds"], 2)
     head = "mixed" if "mixed" in res else "fp64"
     h = res[head]
@@ -320,7 +378,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 inner CG + f64 refinement" if head == "mixed" else "f64",
             "data": "synthetic",
-            "config": {"workload": _workload_desc(prob, p_robin, name),
+            "config": {"workload": _workload_desc(prob, p_robin, name, tc),
                        "precision": (f"mixed: FP32 subdomain CG to {MIXED_INNER_RTOL:g} of the FP64 defect, "
                                      "FP64 defect, exchange and stop test" if head == "mixed" else "FP64"),
                        "l2": "inputs larger than L2 (1.6 GB of subdomain matrices), no flush",
@@ -330,16 +388,23 @@ def run_ours(args):
             "cg_steps_per_solve": h["cg_steps_per_solve"], "relres": h["relres"],
             "setup_s": h["setup_s"], "e2e": h["e2e"], "clocks": h["clocks"]}
     if head == "mixed":
-        line["roofline"] = _roofline(sols["mixed"], 1, "k_cg_spmv<float> (batched SELL-32 FP32 SpMV, 64 subdomains)")
+        line["roofline"] = _roofline(sols["mixed"], 2, "k_cg_spmv_dir32 (batched SELL-32 FP32 SpMV of the CG step "
+                                                        "+ direction epilogue, every subdomain active)")
     else:
-        line["roofline"] = _roofline(sols["fp64"], 0, "k_cg_spmv<double> (batched SELL-32 FP64 SpMV, 64 subdomains)")
+        line["roofline"] = _roofline(sols["fp64"], 3, "k_cg_spmv<double> (batched SELL-32 FP64 SpMV of the CG step, "
+                                                       "every subdomain active)")
     keys = ("value", "ms_per_step", "schwarz_iterations", "cg_steps_per_solve", "relres", "gpu_launches", "e2e",
             "clocks", "setup_s")
     if "fp64" in res and head != "fp64":
         f = res["fp64"]
+        # the mixed solution against the FP64 GPU solution of the same problem (both to rtol)
+        import torch
+        d = torch.linalg.norm(h["_phi"] - f["_phi"]) / torch.linalg.norm(f["_phi"])
+        line["mixed_vs_fp64_rel_l2"] = float(d)
         line["fp64"] = {k: f[k] for k in keys}
         line["fp64"]["precision"] = f"FP64, subdomain PCG to {INNER_RTOL:g} of ||b_i|| every iteration (Sec. 6)"
-        line["fp64"]["roofline"] = _roofline(sols["fp64"], 0, "k_cg_spmv<double> (batched SELL-32 FP64 SpMV)")
+        line["fp64"]["roofline"] = _roofline(sols["fp64"], 3, "k_cg_spmv<double> (batched SELL-32 FP64 SpMV of the "
+                                                               "CG step, every subdomain active)")
         line["mixed_speedup_vs_fp64"] = round(h["value"] / f["value"], 3)
     if "fp64_refine" in res:
         f = res["fp64_refine"]
@@ -348,9 +413,12 @@ def run_ours(args):
                                             f"{MIXED_INNER_RTOL:g} of each iteration's defect")
         if head == "mixed":
             line["mixed_speedup_vs_fp64_refine"] = round(h["value"] / f["value"], 3)
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not _is_slab(name):
         n_outer = res["fp64"]["schwarz_iterations"] if "fp64" in res else _reference_iterations()
         line["cpu_baseline"] = _cpu_baseline(prob, p_robin, n_outer, name)
+    if _is_slab(name):
+        line["cpu_baseline"] = None   # one oracle Schwarz iteration of a 19.5M-node slab run takes far too long
+        line["table2_iterations"] = {"slab32": 41, "slab64": 45, "slab128": 92}[name]
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -384,8 +452,9 @@ def run_batch(args, pkg, ws, rank, local, barrier):
             launches += bs.stats()["n_launches"]
         ev1.record(stream)
         torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    line = {"metric": METRIC, "value": ws * dofs / (ms / 1e3), "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
+    ms_local = ev0.elapsed_time(ev1) / args.steps
+    value, ms = aggregate_over_ranks(ms_local, dofs, device="cuda")
+    line = {"metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32 inner CG + f64 refinement" if prec == "mixed" else "f64",
             "data": "synthetic",
@@ -396,7 +465,106 @@ def run_batch(args, pkg, ws, rank, local, barrier):
             "gpu_launches": int(launches), "schwarz_iterations_min_max": [int(iters.min()), int(iters.max())],
             "relres_max": float(rel.max()), "setup_s": round(bs.info["setup_seconds"], 2),
             "clocks": clk.summary(),
-            "roofline": _roofline(bs, 1 if prec == "mixed" else 0, "batched SELL-32 SpMV, 512 subdomains")}
+            "roofline": _roofline(bs, 2 if prec == "mixed" else 3, "CG-step SELL-32 SpMV kernel, 512 subdomains")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_sample(args, pkg, ws, rank, local, barrier):
+    """Batched p evaluation (Sec. 4): 32 candidates p ~ logU[0.5, 200]
+    (SplitMix64, seed 0) on layered64, every candidate its own Schwarz run to
+    1e-8 (at most 400 iterations), one batched solve sharing the matrices."""
+    import numpy as np
+    import torch
+
+    import gen
+    prob = gen.workload(WORKLOAD)
+    prec = "mixed" if args.prec == "both" else args.prec
+    sol = pkg.Solver.from_problem(prob, p=P_ROBIN, inner_rtol=INNER_RTOL, mixed_inner_rtol=MIXED_INNER_RTOL,
+                                  max_outer=5000, prec=prec)
+    ps = gen.log_uniform_p(0, 32, 0.5, 200.0)
+    max_outer = 400
+    for _ in range(max(args.warmup, 1)):
+        sol.sample_p(ps, rtol=RTOL, max_outer=max_outer)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            iters, rel, best = sol.sample_p(ps, rtol=RTOL, max_outer=max_outer)
+            launches += sol.stats()["n_launches"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms_local = ev0.elapsed_time(ev1) / args.steps
+    st = sol.stats()
+    # DOF/s: unknowns x candidates solved per second (a candidate that hits
+    # the cap counts as evaluated; its run is part of the search)
+    value, ms = aggregate_over_ranks(ms_local, prob.n_dofs * len(ps), device="cuda")
+    conv = rel <= RTOL
+    line = {"metric": "candidate-DOF/s of the batched p evaluation (32 candidates x unknowns / s)",
+            "value": value, "unit": "DOF/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inner CG + f64 refinement" if prec == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": f"sample32: {_workload_desc(prob, 0.0)}; 32 p ~ logU[0.5, 200] (SplitMix64 "
+                                   f"seed 0), each to {RTOL:g} or {max_outer} iterations, one batched solve",
+                       "precision": prec},
+            "gpu_launches": int(launches), "best_p": float(ps[best]), "best_iterations": int(iters[best]),
+            "converged": int(conv.sum()), "iterations": [int(v) for v in iters],
+            "cg_steps": st["n_cg_steps"], "clocks": clk.summary()}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_grad(args, pkg, ws, rank, local, barrier):
+    """Adjoint gradient (config-4 shape): layered48 (48^3 Q2, 3x3x3), 64 x 64
+    surface stations, J = 1/2 ||g_z - g_obs||^2 with g_obs from the density
+    plus N(0, 20^2) per element; one forward solve, one adjoint solve and the
+    element gradient per step."""
+    import numpy as np
+    import torch
+
+    import gen
+    prob = gen.workload("layered48")
+    prec = "mixed" if args.prec == "both" else args.prec
+    sol = pkg.Solver.from_problem(prob, p=P_FOR["layered48"], inner_rtol=INNER_RTOL,
+                                  mixed_inner_rtol=MIXED_INNER_RTOL, max_outer=5000, prec=prec)
+    st_xyz = gen.surface_stations(64)
+    sol.set_stations(st_xyz)
+    rng = np.random.default_rng(0)
+    drho_obs = prob.drho + rng.normal(0.0, 20.0, size=prob.drho.shape)
+    drho_obs_t = torch.from_numpy(drho_obs).cuda()
+    drho_t = torch.from_numpy(prob.drho).cuda()
+    sol.set_density_dev(drho_obs_t)
+    phi_obs, _, _ = sol.solve(RTOL)
+    g_obs = sol.gravity(phi_obs).clone()
+    sol.set_density_dev(drho_t)
+    for _ in range(max(args.warmup, 1)):
+        J, dJ, _ = sol.grad(g_obs, rtol=RTOL)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            J, dJ, _ = sol.grad(g_obs, rtol=RTOL)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms_local = ev0.elapsed_time(ev1) / args.steps
+    value, ms = aggregate_over_ranks(ms_local, 1.0, device="cuda")
+    line = {"metric": "adjoint gradients per second (forward solve + adjoint solve + dJ/d drho)",
+            "value": value, "unit": "gradients/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 inner CG + f64 refinement" if prec == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": f"grad48: {_workload_desc(prob, P_FOR['layered48'], 'layered48')}; "
+                                   f"64x64 stations on the top face, g_obs from drho + N(0, 20^2)",
+                       "precision": prec},
+            "J": float(J), "grad_norm": float(torch.linalg.norm(dJ)), "clocks": clk.summary()}
     if rank == 0:
         print(json.dumps(line), flush=True)
     return 0
@@ -449,7 +617,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prec", choices=("both", "mixed", "fp64"), default="both")
     ap.add_argument("--workload", default=None,
-                    help="profiling runs only: another named workload (e.g. layered48)")
+                    help="another workload: layered48, regional, layered160, slab32/64/128, batch64 "
+                         "(independent problems), sample32 (batched p evaluation), grad48 (adjoint gradient)")
     ap.add_argument("--launch", choices=("graph", "host"), default="graph",
                     help="host: launch the same kernels one by one (for ncu, which cannot attribute "
                          "kernels inside graphs with conditional nodes)")

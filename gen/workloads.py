@@ -15,6 +15,11 @@ axis-aligned tensor-product meshes:
                        8 x 8 x 3 uneven subdomains from jittered cut planes,
                        Gaussian random field (correlation length 5,
                        sigma = 100) plus a paraboloid basin of -250.
+* ``slab_problem``     the paper's own set-up (Sec. 6): a 250 x 250 x 15 box
+                       partitioned into slabs along x only (32, 64 or 128),
+                       384 x 384 x 16 elements (19.5M Q2 nodes, near the
+                       paper's 19.9M unknowns), layered crust with a buried
+                       crater structure standing in for the measured model.
 
 Everything here is input only: coordinates, per-element densities (x-fastest
 flattening), element-index cut arrays, station coordinates and Robin
@@ -33,7 +38,7 @@ __all__ = [
     "G_NEWTON", "Problem", "uniform_coords", "graded_coords", "equal_cuts",
     "jittered_cuts", "element_centroids", "sphere_density", "layered_density",
     "grf_basin_density", "sphere_problem", "layered_problem",
-    "regional_problem", "batch_instances", "surface_stations",
+    "regional_problem", "batch_instances", "surface_stations", "crater_density", "slab_problem",
     "splitmix64", "log_uniform_p", "workload", "WORKLOADS",
 ]
 
@@ -189,6 +194,37 @@ def grf_basin_density(xc, yc, zc, rng, ell=5.0, sigma=100.0,
     return f.ravel()
 
 
+def crater_density(xc, yc, zc, rng, centre=(125.0, 125.0), rim_radius=100.0, cover=1.0,
+                   lens_depth=3.0, lens_value=-250.0, uplift_radius=25.0, uplift_top=4.0,
+                   uplift_bottom=11.0, uplift_value=200.0, ring=(35.0, 45.0), ring_value=100.0,
+                   layers=(100.0, 0.0, -150.0), noise=10.0):
+    """Layered crust with a buried impact structure, in km (top at zc[-1]).
+
+    Layers (bottom third, middle third, top third): ``layers``.  Under a
+    sediment cover of ``cover``: a low-density breccia lens filling the bowl
+    top - cover - lens_depth (1 - r^2/R^2) < z < top - cover inside the rim
+    radius R; a dense central uplift (r < uplift_radius, depths uplift_top to
+    uplift_bottom below the surface); a peak ring (ring[0] < r < ring[1]) in
+    the lens.  Plus white noise N(0, noise^2) per element.
+    """
+    X, Y, Z = element_centroids(xc, yc, zc)
+    lz = zc[-1] - zc[0]
+    t = (Z - zc[0]) / lz
+    rho = np.where(t < 1.0 / 3.0, layers[0], np.where(t < 2.0 / 3.0, layers[1], layers[2]))
+    top = zc[-1]
+    r2 = (X - centre[0]) ** 2 + (Y - centre[1]) ** 2
+    depth = top - Z
+    lens = (r2 < rim_radius ** 2) & (depth > cover) & \
+           (depth < cover + lens_depth * (1.0 - r2 / rim_radius ** 2))
+    rho = np.where(lens, lens_value, rho)
+    ring_m = lens & (r2 > ring[0] ** 2) & (r2 < ring[1] ** 2)
+    rho = np.where(ring_m, ring_value, rho)
+    uplift = (r2 < uplift_radius ** 2) & (depth > uplift_top) & (depth < uplift_bottom)
+    rho = np.where(uplift, uplift_value, rho)
+    rho = rho + rng.normal(0.0, noise, size=rho.shape)
+    return rho.ravel()
+
+
 # ---------------------------------------------------------------- problems --
 
 def sphere_problem(n: int = 16, s: int = 2, p: float = 10.0) -> Problem:
@@ -222,6 +258,20 @@ def regional_problem(nx=128, ny=128, nz=48, sx=8, sy=8, sz=3, p=1.0, seed=0,
                              basin_centre=(0.5 * lx, 0.5 * ly))
     return Problem(f"regional_{nx}x{ny}x{nz}_{sx}x{sy}x{sz}", xc, yc, zc, drho,
                    cx, cy, cz, p=p, rtol=1e-8)
+
+
+def slab_problem(nx=384, ny=384, nz=16, n_slabs=32, seed=0, lx=250.0, ly=250.0, lz=15.0,
+                 p=1.0) -> Problem:
+    """The paper's partition (Sec. 6): slabs along x only, one per subdomain,
+    on a thin 250 x 250 x 15 box; stop test 1e-6 as in Table 2."""
+    rng = np.random.default_rng(seed)
+    xc = uniform_coords(nx, lx)
+    yc = uniform_coords(ny, ly)
+    zc = uniform_coords(nz, lz)
+    drho = crater_density(xc, yc, zc, rng, centre=(0.5 * lx, 0.5 * ly), rim_radius=0.4 * lx)
+    return Problem(f"slab_{nx}x{ny}x{nz}_{n_slabs}", xc, yc, zc, drho,
+                   equal_cuts(nx, n_slabs), np.array([0, ny], dtype=np.int32),
+                   np.array([0, nz], dtype=np.int32), p=p, rtol=1e-6)
 
 
 def batch_instances(n_inst=64, lo=24, hi=40, seed=0, p_lo=2.0, p_hi=50.0):
@@ -287,7 +337,10 @@ def workload(name: str) -> Problem:
         return regional_problem()
     if name == "layered160":
         return layered_problem(160, 8, p=10.0, seed=0)
+    if name in ("slab32", "slab64", "slab128"):
+        return slab_problem(n_slabs=int(name[4:]))
     raise KeyError(name)
 
 
-WORKLOADS = ("sphere16", "layered32", "layered64", "layered48", "regional", "layered160")
+WORKLOADS = ("sphere16", "layered32", "layered64", "layered48", "regional", "layered160",
+             "slab32", "slab64", "slab128")

@@ -97,7 +97,16 @@ typedef struct {
                                device-side while loops; 0: host-driven loop (debugging) */
     int32_t max_seconds;    /* device wall-clock limit of one solve (default 900): past it
                                both loops stop and the call returns OSM_E_TIMEOUT */
-    int32_t reserved[4];
+    int32_t autotune;       /* 1 (default): at setup, time the SpMV kernel variants (one or
+                               two SELL slices per warp, 32- or 16-bit columns) on this
+                               handle's matrices and keep the fastest per precision; 0: one
+                               slice per warp; 2: two slices per warp (no timing) */
+    int32_t index16;        /* 1 (default): when every subdomain has at most 65,536 padded
+                               rows, also store the column indices in 16 bits (FP64: 10
+                               instead of 12 bytes per nonzero, FP32: 6 instead of 8); the
+                               autotuner picks the width per precision (with autotune != 1
+                               the 16-bit ones are used); 0: always 32 bits */
+    int32_t reserved[2];
 } osm_opts;
 
 typedef struct {
@@ -112,6 +121,15 @@ typedef struct {
     int64_t vec_rows;       /* padded device vector length */
     int64_t device_bytes;   /* device memory held by the handle */
     double setup_seconds;   /* host assembly + upload wall time */
+    int32_t spmv_variant_fp64;   /* SELL slices per warp chosen for the FP64 SpMV */
+    int32_t spmv_variant_fp32;   /* ... for the FP32 SpMV (0 without OSM_MIXED) */
+    double spmv_ms_fp64[2];      /* autotuner timings of the FP64 variants, one / two slices per
+                                    warp, 32-bit columns (ms, 0 if not run) */
+    double spmv_ms_fp32[2];
+    double spmv_ms16_fp64[2];    /* the same with 16-bit columns (0 if not stored or not run) */
+    double spmv_ms16_fp32[2];
+    int32_t col_bytes_fp64;      /* bytes per column index read by the FP64 SpMVs (2 or 4) */
+    int32_t col_bytes_fp32;      /* ... by the FP32 SpMVs (0 without OSM_MIXED) */
 } osm_info_t;
 
 typedef struct {
@@ -156,6 +174,21 @@ osm_status osm_set_robin(osm_handle h, double p);
 osm_status osm_set_robin_sub(osm_handle h, const double *p_sub);
 
 /*
+ * Second-order and unsymmetric transmission conditions (Sec. 3, Table 1).
+ * The operator of a subdomain on a face is A = p + q (-d^2/dtau^2), Fourier
+ * symbol p + q k^2, with weak form p M_G + q S_G (S_G: the face's tangential
+ * Q2 stiffness).  On every interface face the subdomain on the lower side
+ * (smaller coordinate along the face normal) uses (p_lo, q_lo) and the one
+ * on the upper side (p_hi, q_hi); the exchange becomes
+ *   lam_ij <- (p_i + p_j) M_Gij u_j + (q_i + q_j) S_Gij u_j - lam_ji.
+ * p_lo = p_hi, q = 0 is osm_set_robin.  Needs p > 0 and q >= 0, finite
+ * (A_i stays SPD), else OSM_E_ARG.  osm_sample_p still evaluates zeroth-order
+ * symmetric candidates and restores these coefficients afterwards;
+ * osm_grad_p returns OSM_E_STATE while q != 0 or p_lo != p_hi.
+ */
+osm_status osm_set_transmission(osm_handle h, double p_lo, double q_lo, double p_hi, double q_hi);
+
+/*
  * Full Schwarz solve from u = 0, lam = 0 until ||f - K ubar|| <= rtol ||f||.
  * phi: device, n_nodes doubles (may be NULL): the averaged solution ubar on
  * the full node grid.  iters / relres: host (may be NULL): Schwarz iterations
@@ -166,8 +199,9 @@ osm_status osm_solve(osm_handle h, double rtol, double *phi, int32_t *iters, dou
 
 /*
  * Batched stochastic evaluation of Robin parameters (Sec. 4): the n_p
- * candidate values p_host[k] > 0 (host) run the FP64 Schwarz solve of
- * osm_solve in batches of up to 32 candidates that share the subdomain
+ * candidate values p_host[k] > 0 (host) run the Schwarz solve of osm_solve,
+ * in the handle's precision mode (OSM_FP64, OSM_MIXED with the FP32 inner
+ * solve, or OSM_FP64_REFINE), in batches of up to 32 candidates that share the subdomain
  * stiffness matrices K_i (one pass over K_i serves every candidate of the
  * batch), each from u = 0 with its own iterate, Robin data, subdomain CG
  * scalars and convergence mask, until its own relative residual reaches rtol
@@ -220,6 +254,17 @@ osm_status osm_potential_vjp(osm_handle h, double rtol, const double *v, double 
  * dJ/dp of the converged map is 0; *dJ_dp receives that value. */
 osm_status osm_grad(osm_handle h, double rtol, const double *g_obs, double *J, double *dJ_drho,
                     double *dJ_dp);
+
+/* Derivative of the truncated iteration with respect to p.  J_N(p) is the
+ * misfit of the averaged iterate after exactly n_iter Schwarz iterations
+ * from zero (each subdomain solve to opts.inner_rtol); dJ_N/dp is computed
+ * by reverse-mode (adjoint) Schwarz: the iterates are kept, then n_iter
+ * backward steps each apply one adjoint subdomain solve, so the cost is
+ * about one more Schwarz solve.  OSM_FP64 single-problem handles with one p
+ * for all subdomains; stations must be set.  g_obs: device (n_st); J, dJ_dp:
+ * host.  The handle's iterates are reset to zero afterwards; the call
+ * allocates n_iter iterate copies for its duration. */
+osm_status osm_grad_p(osm_handle h, int32_t n_iter, const double *g_obs, double *J, double *dJ_dp);
 
 /* SplitMix64 (Steele, Lea & Flood 2014) log-uniform samples in [lo, hi]:
  * p = exp(log lo + u (log hi - log lo)), u = (x >> 11) * 2^-53, x the k-th
@@ -308,13 +353,30 @@ osm_status osm_host_face_system(const osm_mesh *mesh, const double *drho, const 
                                 int32_t face, int64_t *n, int64_t *nnz, int32_t *node,
                                 int64_t *rowptr, int32_t *col, double *val);
 
-/* Time the batched SELL SpMV kernel alone: y = A x over every subdomain
- * (the operator of the CG step).  prec 0: FP64 values and vectors; prec 1:
- * the FP32 operator of the mixed inner solve (OSM_MIXED handles only, else
- * OSM_E_STATE).  After 20 untimed launches, 5 trials of `reps` back-to-back
- * launches are timed with CUDA events on the handle's stream; *ms receives
- * the median time per launch in milliseconds (host).  Uses the stop test's
- * and the inner solve's work vectors; the iterates are not changed. */
+/*
+ * osm_host_local_system_tc: as osm_host_local_system with the transmission
+ * coefficients tc = {p_lo, q_lo, p_hi, q_hi} of osm_set_transmission (host,
+ * 4 values).  osm_host_face_stiffness: the tangential stiffness S_G of face
+ * `face`, nnz values (host) in the CSR order of osm_host_face_system.
+ */
+osm_status osm_host_local_system_tc(const osm_mesh *mesh, const double *drho, const osm_decomp *dec,
+                                    const double *tc, int32_t sub, int64_t *n, int64_t *nnz, int64_t *rowptr,
+                                    int32_t *col, double *val, double *f);
+osm_status osm_host_face_stiffness(const osm_mesh *mesh, const double *drho, const osm_decomp *dec, int32_t face,
+                                   double *val);
+
+/* Time one batched SELL SpMV kernel alone over every subdomain.
+ *   prec 0: the plain FP64 operator y = A x (the stop test's SpMV);
+ *   prec 1: the plain FP32 operator of the mixed inner solve;
+ *   prec 2: the FP32 CG-step kernel k_cg_spmv_dir32 (SpMV of z plus the
+ *           p, q direction epilogue and the p.q partials);
+ *   prec 3: the FP64 CG-step kernel k_cg_spmv<double> (SpMV of p, p.q).
+ * 1 and 2 need an OSM_MIXED handle (else OSM_E_STATE).  After 20 untimed
+ * launches, 5 trials of `reps` back-to-back launches are timed with CUDA
+ * events on the handle's stream; *ms receives the median time per launch in
+ * milliseconds (host).  0 and 1 use the work vectors only; 2 and 3 mark
+ * every subdomain active and overwrite the CG vectors and scalars, so call
+ * them between solves (the next osm_solve starts afresh). */
 osm_status osm_profile_spmv(osm_handle h, int32_t prec, int32_t reps, double *ms);
 
 /*

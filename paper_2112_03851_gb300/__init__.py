@@ -6,5 +6,5 @@ the solver without it raises ImportError -- there is no CPU fallback.
 """
 from ._lib import (  # noqa: F401
     BatchSolver, EXPORTED, LIB_PATH, OSM_FP64, OSM_MIXED, OsmError, Solver, default_opts, gravity_misfit,
-    gravity_potential, host_face_system, host_local_system, load, log_uniform_p,
+    gravity_potential, host_face_stiffness, host_face_system, host_local_system, load, log_uniform_p,
 )

@@ -20,9 +20,10 @@ EXPORTED = (
     "osm_set_robin_sub", "osm_solve", "osm_sample_p", "osm_log_uniform_p", "osm_apply",
     "osm_apply_noalloc", "osm_reset", "osm_iterate", "osm_get_local", "osm_get_lambda",
     "osm_set_lambda", "osm_inner_iters", "osm_stats", "osm_set_density_dev", "osm_set_stations",
-    "osm_gravity", "osm_potential_vjp", "osm_grad", "osm_host_local_system", "osm_host_face_system",
+    "osm_gravity", "osm_potential_vjp", "osm_grad", "osm_grad_p", "osm_host_local_system", "osm_host_face_system",
     "osm_profile_spmv", "osm_status_string", "osm_last_error", "osm_destroy", "osm_setup_batch",
-    "osm_batch_info", "osm_set_robin_inst", "osm_solve_batch",
+    "osm_batch_info", "osm_set_robin_inst", "osm_solve_batch", "osm_set_transmission",
+    "osm_host_local_system_tc", "osm_host_face_stiffness",
 )
 
 
@@ -39,7 +40,8 @@ class OsmDecomp(C.Structure):
 class OsmOpts(C.Structure):
     _fields_ = [("prec", C.c_int32), ("inner_rtol", C.c_double), ("mixed_inner_rtol", C.c_double),
                 ("max_outer", C.c_int32), ("max_inner", C.c_int32), ("use_graph", C.c_int32),
-                ("max_seconds", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("max_seconds", C.c_int32), ("autotune", C.c_int32), ("index16", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class OsmInfo(C.Structure):
@@ -47,7 +49,19 @@ class OsmInfo(C.Structure):
                 ("n_dofs", C.c_int64), ("n_local", C.c_int64), ("n_face_vals", C.c_int64),
                 ("nnz", C.c_int64), ("sell_entries", C.c_int64), ("n_slices", C.c_int64),
                 ("vec_rows", C.c_int64),
-                ("device_bytes", C.c_int64), ("setup_seconds", C.c_double)]
+                ("device_bytes", C.c_int64), ("setup_seconds", C.c_double),
+                ("spmv_variant_fp64", C.c_int32), ("spmv_variant_fp32", C.c_int32),
+                ("spmv_ms_fp64", C.c_double * 2), ("spmv_ms_fp32", C.c_double * 2),
+                ("spmv_ms16_fp64", C.c_double * 2), ("spmv_ms16_fp32", C.c_double * 2),
+                ("col_bytes_fp64", C.c_int32), ("col_bytes_fp32", C.c_int32)]
+
+
+def _info_dict(info):
+    out = {}
+    for k, _ in OsmInfo._fields_:
+        v = getattr(info, k)
+        out[k] = list(v) if hasattr(v, "__len__") else v
+    return out
 
 
 class OsmStats(C.Structure):
@@ -81,6 +95,7 @@ def load():
         "osm_set_density": (C.c_int, [vp, vp]),
         "osm_set_robin": (C.c_int, [vp, d]),
         "osm_set_robin_sub": (C.c_int, [vp, vp]),
+        "osm_set_transmission": (C.c_int, [vp, d, d, d, d]),
         "osm_solve": (C.c_int, [vp, d, vp, vp, vp]),
         "osm_sample_p": (C.c_int, [vp, i32, vp, d, i32, vp, vp, vp]),
         "osm_log_uniform_p": (C.c_int, [C.c_uint64, i32, d, d, vp]),
@@ -98,8 +113,11 @@ def load():
         "osm_gravity": (C.c_int, [vp, vp, vp]),
         "osm_potential_vjp": (C.c_int, [vp, d, vp, vp]),
         "osm_grad": (C.c_int, [vp, d, vp, vp, vp, vp]),
+        "osm_grad_p": (C.c_int, [vp, i32, vp, vp, vp]),
         "osm_host_local_system": (C.c_int, [vp, vp, vp, d, i32, vp, vp, vp, vp, vp, vp]),
         "osm_host_face_system": (C.c_int, [vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]),
+        "osm_host_local_system_tc": (C.c_int, [vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]),
+        "osm_host_face_stiffness": (C.c_int, [vp, vp, vp, i32, vp]),
         "osm_profile_spmv": (C.c_int, [vp, i32, i32, vp]),
         "osm_setup_batch": (C.c_int, [i32, vp, vp, vp, vp, vp, vp]),
         "osm_batch_info": (C.c_int, [vp, vp, vp]),
@@ -168,7 +186,7 @@ class Solver:
     (x fastest); ``cx, cy, cz``: element-index cuts of the subdomain grid.
     """
 
-    def __init__(self, xc, yc, zc, drho, cx, cy, cz, p=1.0, stream=None, **opts):
+    def __init__(self, xc, yc, zc, drho, cx, cy, cz, p=1.0, stream=None, tc=None, **opts):
         import torch
         L = load()
         self._torch = torch
@@ -188,17 +206,19 @@ class Solver:
             raise OsmError(st, msg)
         info = OsmInfo()
         L.osm_info(h, C.byref(info))
-        self.info = {k: getattr(info, k) for k, _ in OsmInfo._fields_}
-        if p is not None:
+        self.info = _info_dict(info)
+        if tc is not None:
+            self.set_transmission(*tc)
+        elif p is not None:
             if np.ndim(p) == 0:
                 self.set_robin(float(p))
             else:
                 self.set_robin_sub(p)
 
     @classmethod
-    def from_problem(cls, prob, p=None, **opts):
+    def from_problem(cls, prob, p=None, tc=None, **opts):
         return cls(prob.xc, prob.yc, prob.zc, prob.drho, prob.cx, prob.cy, prob.cz,
-                   p=prob.p if p is None else p, **opts)
+                   p=prob.p if p is None else p, tc=tc, **opts)
 
     # ------------------------------------------------------------ plumbing
     def _check(self, st, allow=()):
@@ -229,6 +249,11 @@ class Solver:
     def set_robin_sub(self, p_sub):
         p_sub = np.ascontiguousarray(p_sub, dtype=np.float64)
         self._check(load().osm_set_robin_sub(self._h, _ptr(p_sub)))
+
+    def set_transmission(self, p_lo: float, q_lo: float, p_hi: float, q_hi: float):
+        """Second-order / unsymmetric condition p + q(-d^2/dtau^2): (p_lo, q_lo)
+        on the lower side of every face, (p_hi, q_hi) on the upper side."""
+        self._check(load().osm_set_transmission(self._h, float(p_lo), float(q_lo), float(p_hi), float(q_hi)))
 
     def set_density(self, drho):
         drho = np.ascontiguousarray(drho, dtype=np.float64).reshape(-1)
@@ -319,6 +344,15 @@ class Solver:
         self._check(load().osm_grad(self._h, float(rtol), _dptr(g_obs), C.byref(J), _dptr(grad), C.byref(dp)))
         return J.value, grad, dp.value
 
+    def grad_p(self, g_obs, n_iter):
+        """(J_N, dJ_N/dp): misfit after exactly n_iter Schwarz iterations from
+        zero and its derivative w.r.t. p by reverse-mode Schwarz."""
+        g_obs = g_obs.detach().to(dtype=self._torch.float64).contiguous()
+        J = C.c_double()
+        dp = C.c_double()
+        self._check(load().osm_grad_p(self._h, int(n_iter), _dptr(g_obs), C.byref(J), C.byref(dp)))
+        return J.value, dp.value
+
     def stats(self):
         st = OsmStats()
         self._check(load().osm_stats(self._h, C.byref(st)))
@@ -330,19 +364,25 @@ class Solver:
         return it
 
     def profile_spmv(self, reps=20, prec=0):
-        """Median time (ms) of one batched SELL SpMV launch (CUDA events);
-        prec 0: FP64, 1: the FP32 operator of the mixed inner solve."""
+        """Median time (ms) of one batched SELL SpMV launch (CUDA events).
+        prec 0: plain FP64 operator; 1: plain FP32 operator (mixed handles);
+        2: the FP32 CG-step kernel k_cg_spmv_dir32 (mixed handles); 3: the FP64
+        CG-step kernel k_cg_spmv<double>.  2 and 3 overwrite the CG state."""
         ms = C.c_double()
         self._check(load().osm_profile_spmv(self._h, int(prec), int(reps), C.byref(ms)))
         return ms.value
 
     def spmv_bytes(self, prec=0):
-        """Algorithmic bytes of one SpMV: per nonzero the value (8 B FP64 or
-        4 B FP32) and its 4 B column, 8 B per slice offset, the input vector
-        read once and the output written once."""
+        """Algorithmic bytes of one launch of profile_spmv's kernel `prec`: per
+        nonzero the value (8 B FP64 or 4 B FP32) and its column index (4 B, or
+        2 B on a handle with 16-bit indices), 8 B per slice offset, the input
+        vector read once and the output written once; the FP32 CG-step kernel
+        (2) also reads p and q and writes p (12 B per row)."""
         i = self.info
-        vb = 8 if prec == 0 else 4
-        return i["nnz"] * (vb + 4) + i["n_slices"] * 8 + i["n_local"] * 2 * vb
+        vb = 8 if prec in (0, 3) else 4
+        cb = i["col_bytes_fp64"] if prec in (0, 3) else (i["col_bytes_fp32"] or 4)
+        extra = 12 * i["n_local"] if prec == 2 else 0
+        return i["nnz"] * (vb + cb) + i["n_slices"] * 8 + i["n_local"] * 2 * vb + extra
 
     def sample_p(self, p_values, rtol=1e-8, max_outer=None):
         p = np.ascontiguousarray(p_values, dtype=np.float64)
@@ -386,7 +426,7 @@ class BatchSolver(Solver):
             raise OsmError(st, msg)
         info = OsmInfo()
         L.osm_info(h, C.byref(info))
-        self.info = {k: getattr(info, k) for k, _ in OsmInfo._fields_}
+        self.info = _info_dict(info)
         self.n_inst = n
         off = np.zeros(n + 1, dtype=np.int64)
         ni = C.c_int32()
@@ -421,21 +461,28 @@ def log_uniform_p(seed: int, n: int, lo: float, hi: float) -> np.ndarray:
     return out
 
 
-def host_local_system(xc, yc, zc, drho, cx, cy, cz, p, sub):
-    """(A_i as scipy CSR, f_i) unpacked from the GPU packing (host only)."""
+def host_local_system(xc, yc, zc, drho, cx, cy, cz, p, sub, tc=None):
+    """(A_i as scipy CSR, f_i) unpacked from the GPU packing (host only);
+    tc = (p_lo, q_lo, p_hi, q_hi) selects the second-order form."""
     import scipy.sparse as sp
     L = load()
     inp = _Inputs(xc, yc, zc, drho, cx, cy, cz)
     n, nnz = C.c_int64(), C.c_int64()
-    args = (C.byref(inp.mesh), _ptr(inp.drho), C.byref(inp.dec), float(p), int(sub))
-    st = L.osm_host_local_system(*args, C.byref(n), C.byref(nnz), None, None, None, None)
+    if tc is None:
+        fn = L.osm_host_local_system
+        args = (C.byref(inp.mesh), _ptr(inp.drho), C.byref(inp.dec), float(p), int(sub))
+    else:
+        tcv = np.ascontiguousarray(tc, dtype=np.float64)
+        fn = L.osm_host_local_system_tc
+        args = (C.byref(inp.mesh), _ptr(inp.drho), C.byref(inp.dec), _ptr(tcv), int(sub))
+    st = fn(*args, C.byref(n), C.byref(nnz), None, None, None, None)
     if st != OSM_OK:
         raise OsmError(st, "host_local_system")
     rp = np.zeros(n.value + 1, dtype=np.int64)
     ci = np.zeros(nnz.value, dtype=np.int32)
     v = np.zeros(nnz.value)
     f = np.zeros(n.value)
-    L.osm_host_local_system(*args, C.byref(n), C.byref(nnz), _ptr(rp), _ptr(ci), _ptr(v), _ptr(f))
+    fn(*args, C.byref(n), C.byref(nnz), _ptr(rp), _ptr(ci), _ptr(v), _ptr(f))
     return sp.csr_matrix((v, ci, rp), shape=(n.value, n.value)), f
 
 
@@ -455,6 +502,18 @@ def host_face_system(xc, yc, zc, drho, cx, cy, cz, face):
     v = np.zeros(nnz.value)
     L.osm_host_face_system(*args, C.byref(n), C.byref(nnz), _ptr(node), _ptr(rp), _ptr(ci), _ptr(v))
     return node, sp.csr_matrix((v, ci, rp), shape=(n.value, n.value))
+
+
+def host_face_stiffness(xc, yc, zc, drho, cx, cy, cz, face):
+    """Tangential stiffness of one face, same CSR as host_face_system."""
+    import scipy.sparse as sp
+    node, Mf = host_face_system(xc, yc, zc, drho, cx, cy, cz, face)
+    inp = _Inputs(xc, yc, zc, drho, cx, cy, cz)
+    v = np.zeros(Mf.nnz)
+    st = load().osm_host_face_stiffness(C.byref(inp.mesh), _ptr(inp.drho), C.byref(inp.dec), int(face), _ptr(v))
+    if st != OSM_OK:
+        raise OsmError(st, "host_face_stiffness")
+    return node, sp.csr_matrix((v, Mf.indices, Mf.indptr), shape=Mf.shape)
 
 
 def _autograd():

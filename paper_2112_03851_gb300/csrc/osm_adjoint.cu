@@ -123,6 +123,105 @@ __global__ void k_density_gradient(DevAdjoint a, const double* __restrict__ w, d
   grad[e] = 4.0 * kPi * kGravity * acc;
 }
 
+// ---- reverse-mode Schwarz (derivative of the N-iteration misfit w.r.t. p)
+//
+// The forward iteration (symmetric p, exact local solves) is
+//   u^n = A(p)^-1 (f + G lam^{n-1}),  lam^n = 2 p E u^n - P lam^{n-1},
+//   J_N = 1/2 ||B S u^N - g_obs||^2,
+// with G the Robin-data gather into the right-hand sides, E the face mass
+// from the sending side, P the swap of the two sides of a face and S the
+// average of the copies.  Its adjoint runs n = N .. 1 with
+//   ubar^N = S^T B^T r,  ubar^n = 2 p E^T lambar^n (n < N),
+//   bbar^n = A^-1 ubar^n,  lambar^{n-1} = G^T bbar^n - P^T lambar^n,
+//   dJ_N/dp = sum_n [ lambar^n . 2 E u^n  -  bbar^n . M_G u^n ].
+
+// out[c] = v_n / c_n on every copy c of node n (the transpose of the average).
+__global__ void k_nodal_split(DevProblem d, const double* __restrict__ v, double* __restrict__ out) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < d.n_nodes; n += stride) {
+    const int32_t c0 = d.cp_ptr[n], c1 = d.cp_ptr[n + 1];
+    for (int32_t c = c0; c < c1; ++c) out[d.cp_idx[c]] = v[n] / (double)(c1 - c0);
+  }
+}
+
+// mu = M_face lam on both sides of every face (face layout).
+__global__ void k_face_mass_lam(DevProblem d, const double* __restrict__ lam, double* __restrict__ mu) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= d.n_fent) return;
+  const int f = d.fent_face[e];
+  const int64_t eo = d.face_eo[f];
+  const int32_t nf = d.face_n[f];
+  double ast = 0.0, ats = 0.0;
+  for (int32_t k = d.fm_ptr[e]; k < d.fm_ptr[e + 1]; ++k) {
+    const int64_t c = d.fm_col[k] - eo;
+    ast = fma(d.fm_val[k], lam[2 * eo + c], ast);
+    ats = fma(d.fm_val[k], lam[2 * eo + nf + c], ats);
+  }
+  mu[2 * eo + (e - eo)] = ast;
+  mu[2 * eo + nf + (e - eo)] = ats;
+}
+
+// ubar = p2 E^T lambar on the interface rows (zero elsewhere, set before):
+// a row sends to the face slot opposite to the one it receives.
+__global__ void k_exchange_transpose(DevProblem d, const int32_t* __restrict__ partner, const double* __restrict__ mu,
+                                     double p2, double* __restrict__ ub) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= d.n_irow) return;
+  double acc = 0.0;
+  for (int32_t e = d.ilam_ptr[k]; e < d.ilam_ptr[k + 1]; ++e) acc += mu[partner[e]];
+  ub[d.irow[k]] = p2 * acc;
+}
+
+// Block partials of lambar . 2 E u (face entries) and of -bbar . M_G u
+// (interface rows); a single-block kernel adds them in order.
+__global__ void k_dp_terms(DevProblem d, const double* __restrict__ lam, const double* __restrict__ u,
+                           const double* __restrict__ bbar, double* __restrict__ part) {
+  __shared__ double sm[1][kTileSlices];
+  double v[1] = {0.0};
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < d.n_fent) {
+    const int f = d.fent_face[i];
+    const int64_t eo = d.face_eo[f];
+    const int32_t nf = d.face_n[f];
+    double mus = 0.0, mut = 0.0;
+    for (int32_t k = d.fm_ptr[i]; k < d.fm_ptr[i + 1]; ++k) {
+      const int32_t c = d.fm_col[k];
+      mus = fma(d.fm_val[k], u[d.fent_row_s[c]], mus);
+      mut = fma(d.fm_val[k], u[d.fent_row_t[c]], mut);
+    }
+    v[0] = 2.0 * (lam[2 * eo + (i - eo)] * mut + lam[2 * eo + nf + (i - eo)] * mus);
+  }
+  const int64_t j = i - d.n_fent;
+  if (j >= 0 && j < d.n_irow) {
+    double mu = 0.0;
+    for (int32_t e = d.im_ptr[j]; e < d.im_ptr[j + 1]; ++e) mu = fma(d.im_val[e], u[d.im_col[e]], mu);
+    v[0] = -bbar[d.irow[j]] * mu;
+  }
+  block_sum<1>(v, sm);
+  if (threadIdx.x == 0) part[blockIdx.x] = v[0];
+}
+
+__global__ void k_sum_parts(const double* __restrict__ part, int64_t n, double* __restrict__ out) {
+  __shared__ double sm[1][kTileSlices];
+  double v[1] = {0.0};
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) v[0] += part[k];
+  block_sum<1>(v, sm);
+  if (threadIdx.x == 0) *out = v[0];
+}
+
+// lambar^{n-1} = G^T bbar - P^T lambar^n on every face entry.
+__global__ void k_lambar_step(DevProblem d, const double* __restrict__ bbar, const double* __restrict__ lam_old,
+                              double* __restrict__ lam_new) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= d.n_fent) return;
+  const int f = d.fent_face[e];
+  const int64_t eo = d.face_eo[f];
+  const int32_t nf = d.face_n[f];
+  const int64_t m = e - eo;
+  lam_new[2 * eo + m] = bbar[d.fent_row_s[e]] - lam_old[2 * eo + nf + m];
+  lam_new[2 * eo + nf + m] = bbar[d.fent_row_t[e]] - lam_old[2 * eo + m];
+}
+
 inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
@@ -163,6 +262,36 @@ cudaError_t launch_density_gradient(const DevProblem& d, const DevAdjoint& a, co
   (void)d;
   const int64_t ne = (int64_t)a.nx * a.ny * a.nz;
   k_density_gradient<<<blocks_for(ne, 256), 256, 0, s>>>(a, w_nodes, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_nodal_split(const DevProblem& d, const double* v, double* out, cudaStream_t s) {
+  k_nodal_split<<<kNodeBlocks, 256, 0, s>>>(d, v, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exchange_adjoint(const DevProblem& d, const int32_t* partner, const double* lam, double* mu,
+                                    double p2, double* ub, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ub, 0, sizeof(double) * d.n_tiles * kTileRows, s);
+  if (e != cudaSuccess || d.n_fent == 0) return e;
+  k_face_mass_lam<<<blocks_for(d.n_fent, 256), 256, 0, s>>>(d, lam, mu);
+  if (d.n_irow) k_exchange_transpose<<<blocks_for(d.n_irow, 256), 256, 0, s>>>(d, partner, mu, p2, ub);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dp_terms(const DevProblem& d, const double* lam, const double* u, const double* bbar, double* part,
+                            double* out, cudaStream_t s) {
+  const int64_t n = d.n_fent + d.n_irow;
+  const unsigned nb = blocks_for(n > 0 ? n : 1, 256);
+  k_dp_terms<<<nb, 256, 0, s>>>(d, lam, u, bbar, part);
+  k_sum_parts<<<1, 256, 0, s>>>(part, nb, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lambar_step(const DevProblem& d, const double* bbar, const double* lam_old, double* lam_new,
+                               cudaStream_t s) {
+  if (d.n_fent == 0) return cudaSuccess;
+  k_lambar_step<<<blocks_for(d.n_fent, 256), 256, 0, s>>>(d, bbar, lam_old, lam_new);
   return cudaGetLastError();
 }
 

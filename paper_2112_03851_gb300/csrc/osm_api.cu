@@ -43,16 +43,24 @@ struct osm_ctx {
   cudaGraphExec_t exec = nullptr;
   DevCtl* ctl_host = nullptr;   // pinned mirror
   std::vector<double> psub_host;
+  std::vector<double> tc_host;  // 4 per subdomain: p_lo, q_lo, p_hi, q_hi
+  bool tc_general = false;      // second-order or unsymmetric coefficients in use
   // batched p evaluation (allocated on the first osm_sample_p call)
   bool mp_ready = false;
   DevSample mp{};
   cudaGraph_t mp_graph = nullptr;
   cudaGraphExec_t mp_exec = nullptr;
   int last_kind = 0;            // 0: single solve / iterate, 1: batched p evaluation
+  double tune_ms[2][4] = {};  // [fp64, fp32][2 c16 + rpl - 1]
   // adjoint gradient (allocated on first use)
   bool adj_ready = false;
   DevAdjoint adj{};
   double* J_dev = nullptr;
+  // reverse-mode Schwarz: partner slot of every received Robin datum, and a
+  // graph that only runs the subdomain solves
+  int32_t* ilam_partner = nullptr;
+  cudaGraph_t ls_graph = nullptr;
+  cudaGraphExec_t ls_exec = nullptr;
 };
 
 namespace {
@@ -105,6 +113,29 @@ osm_status upload_problem(osm_ctx* h) {
   st0[ns] = hp.n_tiles;
   OSM_CUDA(h, upload(h, &sub_tile0, st0));
   d.slice_off = slice_off; d.cols = cols; d.tile_sub = tile_sub; d.sub_tile0 = sub_tile0;
+  // blocks of the FP32 CG update: runs of up to kUpdGroup tiles within a subdomain
+  {
+    std::vector<int64_t> ub;
+    for (size_t si = 0; si < ns; ++si) {
+      const int64_t a0 = st0[si], a1 = st0[si + 1];
+      for (int64_t t = a0; t < a1; t += kUpdGroup) ub.push_back(t);
+    }
+    int64_t* dub;
+    OSM_CUDA(h, upload(h, &dub, ub));
+    d.ub_tile0 = dub;
+    d.n_ublocks = (int64_t)ub.size();
+  }
+  // 16-bit column indices for the single-path SpMVs when every subdomain fits
+  // (the batched p evaluation keeps reading the 32-bit ones)
+  int64_t max_pad = 0;
+  for (const SubInfo& S : hp.sub) max_pad = std::max<int64_t>(max_pad, S.npad);
+  if (h->opts.index16 && max_pad <= 65536) {
+    std::vector<uint16_t> c16(hp.cols.size());
+    for (size_t k = 0; k < c16.size(); ++k) c16[k] = (uint16_t)hp.cols[k];
+    uint16_t* dc16;
+    OSM_CUDA(h, upload(h, &dc16, c16));
+    d.cols16 = dc16;
+  }
   d.n_tiles = hp.n_tiles;
   d.n_sub = hp.nsub;
   for (double** v : {&d.x, &d.r, &d.z, &d.p, &d.q, &d.w, &d.y}) OSM_CUDA(h, dalloc(h, v, nv));
@@ -118,7 +149,8 @@ osm_status upload_problem(osm_ctx* h) {
   DevSubState& st = d.st;
   for (double** v : {&st.rho, &st.alpha, &st.beta, &st.bb, &st.rr}) OSM_CUDA(h, dalloc(h, v, ns));
   for (int32_t** v : {&st.active, &st.iters, &st.status}) OSM_CUDA(h, dalloc(h, v, ns));
-  for (unsigned** v : {&st.cnt_a, &st.cnt_b, &st.cnt_i}) OSM_CUDA(h, dalloc(h, v, ns));
+  OSM_CUDA(h, dalloc(h, &st.sc, ns));
+  OSM_CUDA(h, dalloc(h, &st.isc2, ns));
   for (double** v : {&d.part0, &d.part1, &d.part2}) OSM_CUDA(h, dalloc(h, v, hp.n_tiles));
   // interface rows
   d.n_irow = (int32_t)hp.irow.size();
@@ -138,6 +170,12 @@ osm_status upload_problem(osm_ctx* h) {
   d.irow = irow; d.irow_sub = irow_sub; d.irow_mdiag = irow_mdiag; d.ilam_ptr = ilam_ptr;
   d.ilam = ilam; d.im_ptr = im_ptr; d.im_col = im_col; d.im_val = im_val; d.im_pos = im_pos;
   d.im_kval = im_kval;
+  double *im_tc, *irow_tdiag;
+  OSM_CUDA(h, upload(h, &im_tc, hp.im_tc));
+  OSM_CUDA(h, upload(h, &irow_tdiag, hp.irow_tdiag));
+  d.im_tc = im_tc; d.irow_tdiag = irow_tdiag;
+  OSM_CUDA(h, dalloc(h, &d.tc, 4 * ns));
+  OSM_CUDA(h, dalloc(h, &d.im_t, hp.im_col.size()));
   // faces
   d.n_fent = hp.n_fent;
   int32_t *fent_face, *fent_row_s, *fent_row_t, *fm_ptr, *fm_col, *face_s, *face_t, *face_n;
@@ -149,6 +187,9 @@ osm_status upload_problem(osm_ctx* h) {
   OSM_CUDA(h, upload(h, &fm_ptr, hp.fm_ptr));
   OSM_CUDA(h, upload(h, &fm_col, hp.fm_col));
   OSM_CUDA(h, upload(h, &fm_val, hp.fm_val));
+  double* fs_val;
+  OSM_CUDA(h, upload(h, &fs_val, hp.fs_val));
+  d.fs_val = fs_val;
   OSM_CUDA(h, upload(h, &face_s, hp.face_s));
   OSM_CUDA(h, upload(h, &face_t, hp.face_t));
   OSM_CUDA(h, upload(h, &face_n, hp.face_n));
@@ -178,7 +219,6 @@ osm_status upload_problem(osm_ctx* h) {
   OSM_CUDA(h, dalloc(h, &d.inst_done, hp.n_inst));
   OSM_CUDA(h, dalloc(h, &d.inst_iters, hp.n_inst));
   OSM_CUDA(h, dalloc(h, &d.inst_relres, hp.n_inst));
-  OSM_CUDA(h, dalloc(h, &d.inst_cnt, hp.n_inst));
   OSM_CUDA(h, dalloc(h, &d.rpart, d.n_rblocks));
   OSM_CUDA(h, dalloc(h, &d.rpart2, d.n_rblocks));
   OSM_CUDA(h, dalloc(h, &d.hist, h->opts.max_outer > 0 ? h->opts.max_outer : 1));
@@ -196,11 +236,29 @@ osm_status upload_problem(osm_ctx* h) {
   return OSM_OK;
 }
 
+// Uploads the handle's transmission coefficients (tc_host: p_lo, q_lo, p_hi,
+// q_hi per subdomain; psub_host: the Robin parameter of the zeroth-order
+// symmetric form, used by the batched p evaluation and the p-derivative) and
+// forms the local matrices and Jacobi diagonals.
 osm_status apply_robin(osm_ctx* h) {
   OSM_CUDA(h, cudaMemcpyAsync(h->d.psub, h->psub_host.data(), sizeof(double) * h->hp.nsub,
                               cudaMemcpyHostToDevice, h->stream));
+  OSM_CUDA(h, cudaMemcpyAsync(h->d.tc, h->tc_host.data(), sizeof(double) * 4 * h->hp.nsub,
+                              cudaMemcpyHostToDevice, h->stream));
   OSM_CUDA(h, launch_set_robin(h->d, h->stream));
   return OSM_OK;
+}
+
+// Zeroth-order symmetric Robin condition with parameter p_sub[s] in
+// subdomain s (tc = (p, 0, p, 0)).
+void set_oo0(osm_ctx* h, const std::vector<double>& p_sub) {
+  h->psub_host = p_sub;
+  h->tc_host.assign(4 * p_sub.size(), 0.0);
+  for (size_t s = 0; s < p_sub.size(); ++s) {
+    h->tc_host[4 * s + 0] = p_sub[s];
+    h->tc_host[4 * s + 2] = p_sub[s];
+  }
+  h->tc_general = false;
 }
 
 osm_status mp_alloc(osm_ctx* h) {
@@ -212,6 +270,8 @@ osm_status mp_alloc(osm_ctx* h) {
   OSM_CUDA(h, dalloc(h, &m.lam, 2 * (size_t)hp.n_fent * W));
   for (double** v : {&m.part0, &m.part1, &m.part2}) OSM_CUDA(h, dalloc(h, v, hp.n_tiles * W));
   for (double** v : {&m.rho, &m.alpha, &m.beta, &m.bb, &m.rr}) OSM_CUDA(h, dalloc(h, v, ns * W));
+  OSM_CUDA(h, dalloc(h, &m.sc, ns * W));
+  OSM_CUDA(h, dalloc(h, &m.isc2, ns * W));
   for (int32_t** v : {&m.active, &m.iters}) OSM_CUDA(h, dalloc(h, v, ns * W));
   OSM_CUDA(h, dalloc(h, &m.psamp, W));
   OSM_CUDA(h, dalloc(h, &m.done, W));
@@ -219,6 +279,8 @@ osm_status mp_alloc(osm_ctx* h) {
   OSM_CUDA(h, dalloc(h, &m.relres, W));
   OSM_CUDA(h, dalloc(h, &m.rpart, (size_t)kNodeBlocks * W));
   OSM_CUDA(h, dalloc(h, &m.rpart2, (size_t)kNodeBlocks * W));
+  if (h->opts.prec == OSM_MIXED)
+    for (float** v : {&m.x32, &m.r32, &m.z32, &m.pd32, &m.q32}) OSM_CUDA(h, dalloc(h, v, nv * W));
   std::vector<int32_t> row_irow(nv, -1);
   for (size_t k = 0; k < hp.irow.size(); ++k) row_irow[hp.irow[k]] = (int32_t)k;
   int32_t* ri;
@@ -322,7 +384,8 @@ osm_status build_mp_graph(osm_ctx* h) {
   cudaGraph_t body = po.conditional.phGraph_out[0];
   OSM_CUDA(h, cudaGraphConditionalHandleCreate(&c_in, body, 0, 0));
   OSM_CUDA(h, cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = launch_mp_rhs_init(h->d, h->mp, cs, c_in, 1);
+  const int mixed = h->opts.prec == OSM_MIXED, refine = h->opts.prec != OSM_FP64;
+  cudaError_t e = launch_mp_rhs_init(h->d, h->mp, cs, c_in, 1, mixed, refine);
   cudaGraphNodeParams pi{};
   cudaGraphNode_t n_in = nullptr;
   if (e == cudaSuccess) {
@@ -339,18 +402,111 @@ osm_status build_mp_graph(osm_ctx* h) {
     }
     if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &n_in, nullptr, 1, cudaStreamSetCaptureDependencies);
   }
-  if (e == cudaSuccess) e = launch_mp_exchange_residual(h->d, h->mp, cs, c_out, 1);
+  if (e == cudaSuccess) e = launch_mp_exchange_residual(h->d, h->mp, cs, c_out, 1, mixed);
   cudaGraph_t captured = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
   OSM_CUDA(h, e);
   OSM_CUDA(h, e2);
   cudaGraph_t ibody = pi.conditional.phGraph_out[0];
   OSM_CUDA(h, cudaStreamBeginCaptureToGraph(cs, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-  e = launch_mp_cg_iteration(h->d, h->mp, cs, c_in, 1);
+  e = launch_mp_cg_iteration(h->d, h->mp, cs, c_in, 1, mixed);
   e2 = cudaStreamEndCapture(cs, &captured);
   OSM_CUDA(h, e);
   OSM_CUDA(h, e2);
   OSM_CUDA(h, cudaGraphInstantiate(&h->mp_exec, g, 0));
+  return OSM_OK;
+}
+
+// Autotuner: time each SpMV variant (1 or 2 SELL slices per warp) on this
+// handle's matrices and keep the faster one per precision.
+// Times the plain SpMV of each precision in every variant -- one or two SELL
+// slices per warp, 32- or (if stored) 16-bit columns -- and keeps the fastest.
+// 16-bit columns cut the bytes, but unpacking them costs integer issue slots,
+// which the FP64 SpMV (near the FP64 FMA limit) may not have to spare.
+osm_status autotune_spmv(osm_ctx* h) {
+  const int fixed = h->opts.autotune == 2 ? 2 : 1;
+  const int have16 = h->d.cols16 != nullptr;
+  h->d.rpl64 = fixed;
+  h->d.rpl32 = h->opts.prec == OSM_MIXED ? fixed : 0;
+  h->d.c16_64 = have16;
+  h->d.c16_32 = have16 && h->opts.prec == OSM_MIXED;
+  if (h->opts.autotune != 1) return OSM_OK;
+  cudaEvent_t e0, e1;
+  OSM_CUDA(h, cudaEventCreate(&e0));
+  OSM_CUDA(h, cudaEventCreate(&e1));
+  cudaError_t e = cudaSuccess;
+  for (int prec = 0; prec < (h->opts.prec == OSM_MIXED ? 2 : 1) && e == cudaSuccess; ++prec) {
+    int best_rpl = 1, best_c16 = 0;
+    double best_ms = 1e300;
+    int32_t& rpl_ref = prec == 0 ? h->d.rpl64 : h->d.rpl32;
+    int32_t& c16_ref = prec == 0 ? h->d.c16_64 : h->d.c16_32;
+    for (int c16 = 0; c16 <= have16 && e == cudaSuccess; ++c16)
+      for (int rpl = 1; rpl <= 2 && e == cudaSuccess; ++rpl) {
+        rpl_ref = rpl;
+        c16_ref = c16;
+        auto launch = [&]() {
+          return prec == 0 ? launch_spmv_plain(h->d, h->d.w, h->d.y, h->stream)
+                           : launch_spmv_plain32(h->d, h->d.z32, h->d.q32, h->stream);
+        };
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = launch();
+        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+        for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = launch();
+        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        h->tune_ms[prec][2 * c16 + rpl - 1] = ms / 5.0;
+        if (ms / 5.0 < best_ms) {
+          best_ms = ms / 5.0;
+          best_rpl = rpl;
+          best_c16 = c16;
+        }
+      }
+    rpl_ref = best_rpl;
+    c16_ref = best_c16;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  OSM_CUDA(h, e);
+  return OSM_OK;
+}
+
+// Graph of the subdomain solves alone (x = A_i^-1 b_i from the current x):
+// CG start, then the device-side CG loop.
+osm_status build_lsolve_graph(osm_ctx* h) {
+  if (h->ls_exec) return OSM_OK;
+  cudaStream_t cs = h->cap_stream;
+  OSM_CUDA(h, cudaGraphCreate(&h->ls_graph, 0));
+  cudaGraphConditionalHandle c_in;
+  OSM_CUDA(h, cudaGraphConditionalHandleCreate(&c_in, h->ls_graph, 0, 0));
+  OSM_CUDA(h, cudaStreamBeginCaptureToGraph(cs, h->ls_graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = launch_cg_init(h->d, cs, c_in, 1, 0);
+  cudaGraphNodeParams pi{};
+  cudaGraphNode_t n_in = nullptr;
+  if (e == cudaSuccess) {
+    cudaStreamCaptureStatus cst;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+    if (e == cudaSuccess) {
+      pi.type = cudaGraphNodeTypeConditional;
+      pi.conditional.handle = c_in;
+      pi.conditional.type = cudaGraphCondTypeWhile;
+      pi.conditional.size = 1;
+      e = cudaGraphAddNode(&n_in, h->ls_graph, deps, nullptr, ndeps, &pi);
+    }
+  }
+  cudaGraph_t captured = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+  OSM_CUDA(h, e);
+  OSM_CUDA(h, e2);
+  OSM_CUDA(h, cudaStreamBeginCaptureToGraph(cs, pi.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal));
+  e = launch_cg_iteration(h->d, cs, c_in, 1);
+  e2 = cudaStreamEndCapture(cs, &captured);
+  OSM_CUDA(h, e);
+  OSM_CUDA(h, e2);
+  OSM_CUDA(h, cudaGraphInstantiate(&h->ls_exec, h->ls_graph, 0));
   return OSM_OK;
 }
 
@@ -478,8 +634,8 @@ osm_status run_sample_batch(osm_ctx* h, int nb, const double* p, double rtol, in
   OSM_CUDA(h, cudaMemsetAsync(m.x, 0, sizeof(double) * h->hp.vec_rows * W, h->stream));
   if (h->hp.n_fent) OSM_CUDA(h, cudaMemsetAsync(m.lam, 0, sizeof(double) * 2 * h->hp.n_fent * W, h->stream));
   OSM_CUDA(h, launch_mp_start(h->d, m, h->stream));
-  ctl_reset(h, rtol, max_outer);
-  h->ctl_host->tau2 = h->opts.inner_rtol * h->opts.inner_rtol;  // candidates run the FP64 solve
+  ctl_reset(h, rtol, max_outer);  // the candidates run the handle's precision mode
+  const int mixed = h->opts.prec == OSM_MIXED, refine = h->opts.prec != OSM_FP64;
   OSM_CUDA(h, cudaMemcpyAsync(h->d.ctl, h->ctl_host, sizeof(DevCtl), cudaMemcpyHostToDevice, h->stream));
   if (h->opts.use_graph) {
     osm_status st = build_mp_graph(h);
@@ -487,14 +643,14 @@ osm_status run_sample_batch(osm_ctx* h, int nb, const double* p, double rtol, in
     OSM_CUDA(h, cudaGraphLaunch(h->mp_exec, h->stream));
   } else {
     for (int n = 0; n < max_outer; ++n) {
-      OSM_CUDA(h, launch_mp_rhs_init(h->d, m, h->stream, 0, 0));
+      OSM_CUDA(h, launch_mp_rhs_init(h->d, m, h->stream, 0, 0, mixed, refine));
       for (int k = 0; k <= h->opts.max_inner; ++k) {
         OSM_CUDA(h, cudaMemcpyAsync(h->ctl_host, h->d.ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, h->stream));
         OSM_CUDA(h, cudaStreamSynchronize(h->stream));
         if (h->ctl_host->n_active == 0 || h->ctl_host->stop) break;
-        OSM_CUDA(h, launch_mp_cg_iteration(h->d, m, h->stream, 0, 0));
+        OSM_CUDA(h, launch_mp_cg_iteration(h->d, m, h->stream, 0, 0, mixed));
       }
-      OSM_CUDA(h, launch_mp_exchange_residual(h->d, m, h->stream, 0, 0));
+      OSM_CUDA(h, launch_mp_exchange_residual(h->d, m, h->stream, 0, 0, mixed));
       OSM_CUDA(h, cudaMemcpyAsync(h->ctl_host, h->d.ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, h->stream));
       OSM_CUDA(h, cudaStreamSynchronize(h->stream));
       if (h->ctl_host->n_active == 0 || h->ctl_host->stop) break;
@@ -547,6 +703,8 @@ void osm_default_opts(osm_opts* o) {
   o->max_inner = 20000;
   o->use_graph = 1;
   o->max_seconds = 900;
+  o->autotune = 1;
+  o->index16 = 1;
 }
 
 const char* osm_status_string(osm_status s) {
@@ -598,8 +756,10 @@ osm_status osm_setup(const osm_mesh* mesh, const double* drho, const osm_decomp*
   OSM_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   osm_status st = upload_problem(h);
   if (st != OSM_OK) return st;
-  h->psub_host.assign(h->hp.nsub, 1.0);
+  set_oo0(h, std::vector<double>(h->hp.nsub, 1.0));
   st = apply_robin(h);
+  if (st != OSM_OK) return st;
+  st = autotune_spmv(h);
   if (st != OSM_OK) return st;
   OSM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -624,6 +784,16 @@ osm_status osm_info(osm_handle h, osm_info_t* o) {
   o->vec_rows = h->hp.vec_rows;
   o->device_bytes = (int64_t)h->dev_bytes;
   o->setup_seconds = h->setup_seconds;
+  o->spmv_variant_fp64 = h->d.rpl64;
+  o->spmv_variant_fp32 = h->d.rpl32;
+  for (int v = 0; v < 2; ++v) {
+    o->spmv_ms_fp64[v] = h->tune_ms[0][v];
+    o->spmv_ms_fp32[v] = h->tune_ms[1][v];
+    o->spmv_ms16_fp64[v] = h->tune_ms[0][2 + v];
+    o->spmv_ms16_fp32[v] = h->tune_ms[1][2 + v];
+  }
+  o->col_bytes_fp64 = h->d.c16_64 ? 2 : 4;
+  o->col_bytes_fp32 = h->opts.prec == OSM_MIXED ? (h->d.c16_32 ? 2 : 4) : 0;
   return OSM_OK;
 }
 
@@ -642,7 +812,27 @@ osm_status osm_set_density(osm_handle h, const double* drho) {
 osm_status osm_set_robin(osm_handle h, double p) {
   if (!h) return OSM_E_ARG;
   if (!(p > 0.0) || !std::isfinite(p)) return fail(h, OSM_E_ARG, "Robin parameter must be positive and finite");
-  h->psub_host.assign(h->hp.nsub, p);
+  set_oo0(h, std::vector<double>(h->hp.nsub, p));
+  return apply_robin(h);
+}
+
+osm_status osm_set_transmission(osm_handle h, double p_lo, double q_lo, double p_hi, double q_hi) {
+  if (!h) return OSM_E_ARG;
+  for (double p : {p_lo, p_hi})
+    if (!(p > 0.0) || !std::isfinite(p)) return fail(h, OSM_E_ARG, "transmission p must be positive and finite");
+  for (double q : {q_lo, q_hi})
+    if (!(q >= 0.0) || !std::isfinite(q)) return fail(h, OSM_E_ARG, "transmission q must be >= 0 and finite");
+  const int ns = h->hp.nsub;
+  h->tc_host.resize(4 * (size_t)ns);
+  for (int s = 0; s < ns; ++s) {
+    h->tc_host[4 * s + 0] = p_lo;
+    h->tc_host[4 * s + 1] = q_lo;
+    h->tc_host[4 * s + 2] = p_hi;
+    h->tc_host[4 * s + 3] = q_hi;
+  }
+  // psub is read only by the zeroth-order symmetric paths (osm_grad_p checks tc_general)
+  h->psub_host.assign(ns, p_lo);
+  h->tc_general = !(q_lo == 0.0 && q_hi == 0.0 && p_lo == p_hi);
   return apply_robin(h);
 }
 
@@ -651,7 +841,7 @@ osm_status osm_set_robin_sub(osm_handle h, const double* p_sub) {
   for (int s = 0; s < h->hp.nsub; ++s)
     if (!(p_sub[s] > 0.0) || !std::isfinite(p_sub[s]))
       return fail(h, OSM_E_ARG, "Robin parameters must be positive and finite");
-  h->psub_host.assign(p_sub, p_sub + h->hp.nsub);
+  set_oo0(h, std::vector<double>(p_sub, p_sub + h->hp.nsub));
   return apply_robin(h);
 }
 
@@ -712,8 +902,10 @@ osm_status osm_setup_batch(int32_t n_inst, const osm_mesh* meshes, const double*
   OSM_CUDA(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   osm_status st = upload_problem(h);
   if (st != OSM_OK) return st;
-  h->psub_host.assign(h->hp.nsub, 1.0);
+  set_oo0(h, std::vector<double>(h->hp.nsub, 1.0));
   st = apply_robin(h);
+  if (st != OSM_OK) return st;
+  st = autotune_spmv(h);
   if (st != OSM_OK) return st;
   OSM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -736,7 +928,9 @@ osm_status osm_set_robin_inst(osm_handle h, const double* p_inst) {
   for (int i = 0; i < h->hp.n_inst; ++i)
     if (!(p_inst[i] > 0.0) || !std::isfinite(p_inst[i]))
       return fail(h, OSM_E_ARG, "Robin parameters must be positive and finite");
-  for (int s = 0; s < h->hp.nsub; ++s) h->psub_host[s] = p_inst[h->hp.sub_inst[s]];
+  std::vector<double> ps(h->hp.nsub);
+  for (int s = 0; s < h->hp.nsub; ++s) ps[s] = p_inst[h->hp.sub_inst[s]];
+  set_oo0(h, ps);
   return apply_robin(h);
 }
 
@@ -865,9 +1059,8 @@ osm_status osm_sample_p(osm_handle h, int32_t n_p, const double* p_host, double 
   osm_status st = mp_alloc(h);
   if (st != OSM_OK) return st;
   // the batched run needs the plain stiffness K_i in the SELL values
-  std::vector<double> zero(h->hp.nsub, 0.0);
-  OSM_CUDA(h, cudaMemcpyAsync(h->d.psub, zero.data(), sizeof(double) * h->hp.nsub, cudaMemcpyHostToDevice,
-                              h->stream));
+  OSM_CUDA(h, cudaMemsetAsync(h->d.psub, 0, sizeof(double) * h->hp.nsub, h->stream));
+  OSM_CUDA(h, cudaMemsetAsync(h->d.tc, 0, sizeof(double) * 4 * h->hp.nsub, h->stream));
   OSM_CUDA(h, launch_set_robin(h->d, h->stream));
   int status_or = 0;
   for (int32_t b0 = 0; b0 < n_p && st == OSM_OK; b0 += kSampleWidth) {
@@ -1015,9 +1208,125 @@ osm_status osm_grad(osm_handle h, double rtol, const double* g_obs, double* J, d
   return finish_status(h, true, rtol);
 }
 
-osm_status osm_host_local_system(const osm_mesh* mesh, const double* drho, const osm_decomp* dec, double p,
-                                 int32_t sub, int64_t* n, int64_t* nnz, int64_t* rowptr, int32_t* col,
-                                 double* val, double* f) {
+osm_status osm_grad_p(osm_handle h, int32_t n_iter, const double* g_obs, double* J, double* dJ_dp) {
+  if (!h || n_iter < 1 || !g_obs || !J || !dJ_dp) return OSM_E_ARG;
+  if (h->hp.n_inst > 1) return fail(h, OSM_E_STATE, "osm_grad_p needs a single-problem handle");
+  if (h->opts.prec != OSM_FP64) return fail(h, OSM_E_STATE, "osm_grad_p needs an OSM_FP64 handle");
+  if (!h->adj_ready || h->adj.n_st == 0) return fail(h, OSM_E_STATE, "osm_grad_p: call osm_set_stations first");
+  if (n_iter > h->opts.max_outer) return fail(h, OSM_E_ARG, "osm_grad_p: n_iter exceeds max_outer");
+  if (h->tc_general) return fail(h, OSM_E_STATE, "osm_grad_p needs the zeroth-order symmetric Robin condition");
+  for (double q : h->psub_host)
+    if (q != h->psub_host[0]) return fail(h, OSM_E_STATE, "osm_grad_p needs one Robin parameter for all subdomains");
+  h->err.clear();
+  const double p = h->psub_host[0];
+  const size_t nv = h->hp.vec_rows, nl = 2 * (size_t)(h->hp.n_fent ? h->hp.n_fent : 1);
+  if (!h->ilam_partner) {
+    std::vector<int32_t> partner_of(nl, 0);
+    for (int f = 0; f < h->hp.nface; ++f) {
+      const int64_t eo = h->hp.face_eo[f];
+      const int32_t nf = h->hp.face_n[f];
+      for (int32_t m = 0; m < nf; ++m) {
+        partner_of[2 * eo + m] = (int32_t)(2 * eo + nf + m);
+        partner_of[2 * eo + nf + m] = (int32_t)(2 * eo + m);
+      }
+    }
+    std::vector<int32_t> partner(h->hp.ilam.size());
+    for (size_t e = 0; e < partner.size(); ++e) partner[e] = partner_of[h->hp.ilam[e]];
+    OSM_CUDA(h, upload(h, &h->ilam_partner, partner));
+  }
+  osm_status st = build_lsolve_graph(h);
+  if (st != OSM_OK) return st;
+  // temporaries of this call
+  double *uhist = nullptr, *lam_a = nullptr, *lam_b = nullptr, *mu = nullptr, *ub = nullptr, *part = nullptr,
+         *dps = nullptr;
+  const int64_t nparts = (h->hp.n_fent + (int64_t)h->hp.irow.size() + 255) / 256 + 1;
+  auto cleanup = [&]() {
+    for (double* q : {uhist, lam_a, lam_b, mu, ub, part, dps}) if (q) cudaFree(q);
+  };
+  cudaError_t e = cudaMalloc((void**)&uhist, sizeof(double) * nv * (size_t)n_iter);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&lam_a, sizeof(double) * nl);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&lam_b, sizeof(double) * nl);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&mu, sizeof(double) * nl);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&ub, sizeof(double) * nv);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&part, sizeof(double) * nparts);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&dps, sizeof(double) * n_iter);
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(h, e == cudaErrorMemoryAllocation ? OSM_E_NOMEM : OSM_E_CUDA, cudaGetErrorString(e));
+  }
+  // forward: exactly n_iter Schwarz iterations from zero, keeping every iterate
+  h->last_kind = 0;
+  st = reset_state(h);
+  for (int n = 0; n < n_iter && st == OSM_OK; ++n) {
+    st = run_iterations(h, -1.0, 1);
+    if (st == OSM_OK && (h->ctl_host->status & 6)) st = fail(h, OSM_E_BREAKDOWN, "forward Schwarz iteration failed");
+    if (st == OSM_OK) {
+      e = cudaMemcpyAsync(uhist + (size_t)n * nv, h->d.x, sizeof(double) * nv, cudaMemcpyDeviceToDevice, h->stream);
+      if (e != cudaSuccess) st = fail(h, OSM_E_CUDA, cudaGetErrorString(e));
+    }
+  }
+  // misfit of the averaged last iterate and ubar^N = S^T B^T r
+  DevAdjoint& a = h->adj;
+  if (st == OSM_OK) {
+    e = launch_station_values(h->d, a, h->d.phi, g_obs, h->stream);
+    if (e == cudaSuccess) e = launch_misfit(a, h->J_dev, h->stream);
+    if (e == cudaSuccess) e = launch_stations_transpose(h->d, a, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(J, h->J_dev, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ub, 0, sizeof(double) * nv, h->stream);
+    if (e == cudaSuccess) e = launch_nodal_split(h->d, a.v_nodes, ub, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lam_a, 0, sizeof(double) * nl, h->stream);
+    if (e != cudaSuccess) st = fail(h, OSM_E_CUDA, cudaGetErrorString(e));
+  }
+  // backward sweep (bstatus: loop status of every adjoint local solve)
+  std::vector<int32_t> bstatus(n_iter, 0);
+  for (int n = n_iter - 1; n >= 0 && st == OSM_OK; --n) {
+    const double* un = uhist + (size_t)n * nv;
+    if (n < n_iter - 1) e = launch_exchange_adjoint(h->d, h->ilam_partner, lam_a, mu, 2.0 * p, ub, h->stream);
+    // bbar^n = A^-1 ubar^n
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.b, ub, sizeof(double) * nv, cudaMemcpyDeviceToDevice, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->d.x, 0, sizeof(double) * nv, h->stream);
+    if (e != cudaSuccess) { st = fail(h, OSM_E_CUDA, cudaGetErrorString(e)); break; }
+    ctl_reset(h, -1.0, 1);
+    OSM_CUDA(h, cudaMemcpyAsync(h->d.ctl, h->ctl_host, sizeof(DevCtl), cudaMemcpyHostToDevice, h->stream));
+    // the forward pass left the instance marked done; the subdomain solves must run
+    OSM_CUDA(h, cudaMemsetAsync(h->d.inst_done, 0, sizeof(int32_t) * h->hp.n_inst, h->stream));
+    e = cudaGraphLaunch(h->ls_exec, h->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&bstatus[n], &h->d.ctl->status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = launch_dp_terms(h->d, lam_a, un, h->d.x, part, dps + n, h->stream);
+    if (e == cudaSuccess) e = launch_lambar_step(h->d, h->d.x, lam_a, lam_b, h->stream);
+    if (e != cudaSuccess) { st = fail(h, OSM_E_CUDA, cudaGetErrorString(e)); break; }
+    std::swap(lam_a, lam_b);
+  }
+  std::vector<double> terms(n_iter, 0.0);
+  if (st == OSM_OK) {
+    e = cudaMemcpyAsync(terms.data(), dps, sizeof(double) * n_iter, cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h->ctl_host, h->d.ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) st = fail(h, OSM_E_CUDA, cudaGetErrorString(e));
+    int any = 0;
+    for (int32_t b : bstatus) any |= b;
+    if (st == OSM_OK && (any & 4)) st = fail(h, OSM_E_TIMEOUT, "osm_grad_p: adjoint solves exceeded opts.max_seconds");
+    if (st == OSM_OK && (any & 2)) st = fail(h, OSM_E_BREAKDOWN, "osm_grad_p: CG breakdown in an adjoint solve");
+  }
+  // restore the handle: b = f off the interface, zero iterates
+  cudaMemcpyAsync(h->d.b, h->d.f, sizeof(double) * nv, cudaMemcpyDeviceToDevice, h->stream);
+  osm_status st2 = reset_state(h);
+  cudaStreamSynchronize(h->stream);
+  cleanup();
+  if (st != OSM_OK) return st;
+  if (st2 != OSM_OK) return st2;
+  double sum = 0.0;
+  for (int n = 0; n < n_iter; ++n) sum += terms[n];
+  *dJ_dp = sum;
+  return OSM_OK;
+}
+
+// Local system of one subdomain unpacked from the SELL arrays plus the
+// transmission entries: p * M (tc == nullptr) or the split form with tc.
+static osm_status host_local_system(const osm_mesh* mesh, const double* drho, const osm_decomp* dec, double p,
+                                    const double* tc, int32_t sub, int64_t* n, int64_t* nnz, int64_t* rowptr,
+                                    int32_t* col, double* val, double* f) {
   if (!mesh || !drho || !dec || !n || !nnz) return OSM_E_ARG;
   HostProblem hp;
   if (!build_host_problem(*mesh, drho, *dec, hp).empty()) return OSM_E_ARG;
@@ -1042,8 +1351,11 @@ osm_status osm_host_local_system(const osm_mesh* mesh, const double* drho, const
   for (size_t k = 0; k < hp.irow.size(); ++k) {
     if (hp.irow_sub[k] != sub) continue;
     auto& row = rows[v2c[hp.irow[k] - S.voff]];
-    for (int32_t e = hp.im_ptr[k]; e < hp.im_ptr[k + 1]; ++e)
-      row.push_back({v2c[hp.im_col[e] - S.voff], p * hp.im_val[e]});
+    for (int32_t e = hp.im_ptr[k]; e < hp.im_ptr[k + 1]; ++e) {
+      const double* t = hp.im_tc.data() + 4 * (size_t)e;
+      const double a = tc ? tc[0] * t[0] + tc[2] * t[1] + tc[1] * t[2] + tc[3] * t[3] : p * hp.im_val[e];
+      row.push_back({v2c[hp.im_col[e] - S.voff], a});
+    }
   }
   int64_t total = 0;
   for (auto& row : rows) {  // merge duplicates (padding adds zero to the diagonal)
@@ -1068,6 +1380,31 @@ osm_status osm_host_local_system(const osm_mesh* mesh, const double* drho, const
     rowptr[q + 1] = o;
     f[q] = hp.f[hp.can2vec[S.canon_off + q]];
   }
+  return OSM_OK;
+}
+
+osm_status osm_host_local_system(const osm_mesh* mesh, const double* drho, const osm_decomp* dec, double p,
+                                 int32_t sub, int64_t* n, int64_t* nnz, int64_t* rowptr, int32_t* col,
+                                 double* val, double* f) {
+  return host_local_system(mesh, drho, dec, p, nullptr, sub, n, nnz, rowptr, col, val, f);
+}
+
+osm_status osm_host_local_system_tc(const osm_mesh* mesh, const double* drho, const osm_decomp* dec,
+                                    const double* tc, int32_t sub, int64_t* n, int64_t* nnz, int64_t* rowptr,
+                                    int32_t* col, double* val, double* f) {
+  if (!tc) return OSM_E_ARG;
+  return host_local_system(mesh, drho, dec, 0.0, tc, sub, n, nnz, rowptr, col, val, f);
+}
+
+osm_status osm_host_face_stiffness(const osm_mesh* mesh, const double* drho, const osm_decomp* dec, int32_t face,
+                                   double* val) {
+  if (!mesh || !drho || !dec || !val) return OSM_E_ARG;
+  HostProblem hp;
+  if (!build_host_problem(*mesh, drho, *dec, hp).empty()) return OSM_E_ARG;
+  if (face < 0 || face >= hp.nface) return OSM_E_ARG;
+  const int64_t eo = hp.face_eo[face];
+  const int32_t nf = hp.face_n[face];
+  for (int32_t k = hp.fm_ptr[eo]; k < hp.fm_ptr[eo + nf]; ++k) val[k - hp.fm_ptr[eo]] = hp.fs_val[k];
   return OSM_OK;
 }
 
@@ -1103,11 +1440,17 @@ osm_status osm_host_face_system(const osm_mesh* mesh, const double* drho, const 
 }
 
 osm_status osm_profile_spmv(osm_handle h, int32_t prec, int32_t reps, double* ms) {
-  if (!h || !ms || reps < 1 || (prec != 0 && prec != 1)) return OSM_E_ARG;
-  if (prec == 1 && h->opts.prec != OSM_MIXED) return fail(h, OSM_E_STATE, "prec 1 needs an OSM_MIXED handle");
+  if (!h || !ms || reps < 1 || prec < 0 || prec > 3) return OSM_E_ARG;
+  if ((prec == 1 || prec == 2) && h->opts.prec != OSM_MIXED)
+    return fail(h, OSM_E_STATE, "prec 1 and 2 need an OSM_MIXED handle");
+  if (prec >= 2) OSM_CUDA(h, launch_profile_state(h->d, h->stream));
   auto launch = [&]() {
-    return prec == 0 ? launch_spmv_plain(h->d, h->d.w, h->d.y, h->stream)
-                     : launch_spmv_plain32(h->d, h->d.z32, h->d.q32, h->stream);
+    switch (prec) {
+      case 0: return launch_spmv_plain(h->d, h->d.w, h->d.y, h->stream);
+      case 1: return launch_spmv_plain32(h->d, h->d.z32, h->d.q32, h->stream);
+      case 2: return launch_cg_spmv_alone(h->d, 1, h->stream);
+      default: return launch_cg_spmv_alone(h->d, 0, h->stream);
+    }
   };
   cudaEvent_t e0, e1;
   OSM_CUDA(h, cudaEventCreate(&e0));
@@ -1138,6 +1481,8 @@ void osm_destroy(osm_handle h) {
   if (h->graph) cudaGraphDestroy(h->graph);
   if (h->mp_exec) cudaGraphExecDestroy(h->mp_exec);
   if (h->mp_graph) cudaGraphDestroy(h->mp_graph);
+  if (h->ls_exec) cudaGraphExecDestroy(h->ls_exec);
+  if (h->ls_graph) cudaGraphDestroy(h->ls_graph);
   cudaStreamSynchronize(h->stream);
   for (void* p : h->allocs) cudaFree(p);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);

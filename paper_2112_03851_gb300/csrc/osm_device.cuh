@@ -17,9 +17,10 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Sum NV values over the 256 threads of a block; result valid in thread 0.
-template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sm)[kTileSlices]) {
+// Sum NV values over the NW warps of a block; result valid in thread 0.
+template <int NV, int NW = kTileSlices, int SW = kTileSlices>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double (*sm)[SW]) {
+  static_assert(NW <= SW, "shared scratch narrower than the warp count");
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int k = 0; k < NV; ++k) {
@@ -32,18 +33,26 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sm)[kTileSli
     for (int k = 0; k < NV; ++k) {
       double s = 0.0;
 #pragma unroll
-      for (int w = 0; w < kTileSlices; ++w) s += sm[k][w];
+      for (int w = 0; w < NW; ++w) s += sm[k][w];
       v[k] = s;
     }
   }
 }
 
 // Sum of part[t0 .. t0+nt) in a fixed order by one warp (all lanes get it).
+// Four independent loads per lane per step keep several L2 requests in flight.
 __device__ __forceinline__ double warp_sum_parts(const double* part, int64_t t0, int64_t nt) {
   const int lane = threadIdx.x & 31;
-  double v = 0.0;
-  for (int64_t k = lane; k < nt; k += 32) v += __ldcg(part + t0 + k);
-  return warp_sum(v);
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+  int64_t k = lane;
+  for (; k + 96 < nt; k += 128) {
+    v0 += __ldcg(part + t0 + k);
+    v1 += __ldcg(part + t0 + k + 32);
+    v2 += __ldcg(part + t0 + k + 64);
+    v3 += __ldcg(part + t0 + k + 96);
+  }
+  for (; k < nt; k += 32) v0 += __ldcg(part + t0 + k);
+  return warp_sum((v0 + v1) + (v2 + v3));
 }
 
 // One row of a SELL-32 slice: lane `lane` of the warp owning the slice at
@@ -88,6 +97,126 @@ __device__ __forceinline__ float sell_row(const int32_t* __restrict__ cols, cons
     acc1 = fmaf(a.w, __ldg(x + c.w), acc1);
   }
   return acc0 + acc1;
+}
+
+// Rows of one 256-row tile handled by the calling thread when each warp works
+// RPL slices at once (blockDim = 256 / RPL): slice tile*8 + warp*RPL + k,
+// row slice*32 + lane.  The slices' loads are interleaved step by step, so a
+// lane keeps RPL independent streams in flight.  FP64 values use the pair
+// layout (two double2 per step), FP32 values the quad layout (one float4).
+template <class T, int RPL>
+__device__ __forceinline__ void tile_rows(const int64_t* __restrict__ slice_off, const int32_t* __restrict__ cols,
+                                          const T* __restrict__ vals, int64_t tile, const T* __restrict__ x,
+                                          T (&y)[RPL], int64_t (&row)[RPL]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t off[RPL];
+  int nq[RPL];
+  int nqmax = 0;
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) {
+    const int64_t slice = tile * kTileSlices + warp * RPL + k;
+    off[k] = slice_off[slice];
+    nq[k] = (int)((slice_off[slice + 1] - off[k]) >> 7);  // width / 4
+    row[k] = slice * kSliceRows + lane;
+    nqmax = max(nqmax, nq[k]);
+  }
+  T a0[RPL], a1[RPL];
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) { a0[k] = T(0); a1[k] = T(0); }
+#pragma unroll 2
+  for (int q = 0; q < nqmax; ++q) {
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      if (q < nq[k]) {
+        const int4 c = __ldcs(reinterpret_cast<const int4*>(cols + off[k]) + lane + q * 32);
+        if constexpr (sizeof(T) == 8) {
+          const double2* v2 = reinterpret_cast<const double2*>(vals + off[k]) + lane;
+          const double2 a = __ldcs(v2 + q * 64);
+          const double2 b = __ldcs(v2 + q * 64 + 32);
+          a0[k] = fma(a.x, __ldg(x + c.x), a0[k]);
+          a1[k] = fma(a.y, __ldg(x + c.y), a1[k]);
+          a0[k] = fma(b.x, __ldg(x + c.z), a0[k]);
+          a1[k] = fma(b.y, __ldg(x + c.w), a1[k]);
+        } else {
+          const float4 a = __ldcs(reinterpret_cast<const float4*>(vals + off[k]) + lane + q * 32);
+          a0[k] = fmaf(a.x, __ldg(x + c.x), a0[k]);
+          a1[k] = fmaf(a.y, __ldg(x + c.y), a1[k]);
+          a0[k] = fmaf(a.z, __ldg(x + c.z), a0[k]);
+          a1[k] = fmaf(a.w, __ldg(x + c.w), a1[k]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) y[k] = a0[k] + a1[k];
+}
+
+// Rows of one tile with 16-bit column indices (subdomains of at most 65,536
+// padded rows): the same layouts, but lane l of step q loads its four
+// columns as one 8-byte uint2 at entry off + 128 q + 4 l (2 instead of 4
+// bytes per nonzero).  Same per-row summation order as tile_rows.
+template <class T, int RPL>
+__device__ __forceinline__ void tile_rows16(const int64_t* __restrict__ slice_off, const uint16_t* __restrict__ cols,
+                                            const T* __restrict__ vals, int64_t tile, const T* __restrict__ x,
+                                            T (&y)[RPL], int64_t (&row)[RPL]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int64_t off[RPL];
+  int nq[RPL];
+  int nqmax = 0;
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) {
+    const int64_t slice = tile * kTileSlices + warp * RPL + k;
+    off[k] = slice_off[slice];
+    nq[k] = (int)((slice_off[slice + 1] - off[k]) >> 7);
+    row[k] = slice * kSliceRows + lane;
+    nqmax = max(nqmax, nq[k]);
+  }
+  T a0[RPL], a1[RPL];
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) { a0[k] = T(0); a1[k] = T(0); }
+#pragma unroll 2
+  for (int q = 0; q < nqmax; ++q) {
+#pragma unroll
+    for (int k = 0; k < RPL; ++k) {
+      if (q < nq[k]) {
+        const uint2 c = __ldcs(reinterpret_cast<const uint2*>(cols + off[k]) + lane + q * 32);
+        const unsigned c0 = c.x & 0xffffu, c1 = c.x >> 16, c2 = c.y & 0xffffu, c3 = c.y >> 16;
+        if constexpr (sizeof(T) == 8) {
+          const double2* v2 = reinterpret_cast<const double2*>(vals + off[k]) + lane;
+          const double2 a = __ldcs(v2 + q * 64);
+          const double2 b = __ldcs(v2 + q * 64 + 32);
+          a0[k] = fma(a.x, __ldg(x + c0), a0[k]);
+          a1[k] = fma(a.y, __ldg(x + c1), a1[k]);
+          a0[k] = fma(b.x, __ldg(x + c2), a0[k]);
+          a1[k] = fma(b.y, __ldg(x + c3), a1[k]);
+        } else {
+          const float4 a = __ldcs(reinterpret_cast<const float4*>(vals + off[k]) + lane + q * 32);
+          a0[k] = fmaf(a.x, __ldg(x + c0), a0[k]);
+          a1[k] = fmaf(a.y, __ldg(x + c1), a1[k]);
+          a0[k] = fmaf(a.z, __ldg(x + c2), a0[k]);
+          a1[k] = fmaf(a.w, __ldg(x + c3), a1[k]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) y[k] = a0[k] + a1[k];
+}
+
+// Dispatch on the column width chosen at setup (C16: d.cols16).
+template <class T, int RPL, bool C16>
+__device__ __forceinline__ void tile_rows_any(const DevProblem& d, const T* __restrict__ vals, int64_t tile,
+                                              const T* __restrict__ x, T (&y)[RPL], int64_t (&row)[RPL]) {
+  if constexpr (C16) tile_rows16<T, RPL>(d.slice_off, d.cols16, vals, tile, x, y, row);
+  else tile_rows<T, RPL>(d.slice_off, d.cols, vals, tile, x, y, row);
+}
+
+// Mean of c copies, s / c.  On a box grid of subdomains a node has 1, 2, 4
+// or 8 copies: then s * 2^-k, which is bit-identical to the division and
+// avoids FP64 division (a long instruction sequence on this GPU).
+__device__ __forceinline__ double copy_mean(double s, int c) {
+  if ((c & (c - 1)) == 0) return s * __longlong_as_double((long long)(1023 - (__ffs(c) - 1)) << 52);
+  return s / (double)c;
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {

@@ -16,6 +16,10 @@ namespace osm {
 constexpr int kSliceRows = 32;
 constexpr int kTileRows = 256;
 constexpr int kTileSlices = kTileRows / kSliceRows;
+// Tiles per block of the FP32 CG update (all of one subdomain).
+constexpr int kUpdGroup = 8;
+// Threads of the one-block stop-test finaliser.
+constexpr int kResFinThreads = 1024;
 // SELL row widths are padded to a multiple of 4 so that every lane can load
 // four column indices (int4) and two value pairs (double2) per step.
 constexpr int kWidthQuantum = 4;
@@ -75,6 +79,11 @@ struct HostProblem {
   std::vector<int64_t> im_pos;        // position of the entry in the SELL value array
   std::vector<double> im_kval;        // K_i value at that position
   std::vector<int64_t> im_pos32;      // position in the FP32 value array
+  // Second-order / unsymmetric transmission: the same entries split by the
+  // side of the face (lower: this subdomain has the smaller coordinate along
+  // the face normal) into face mass and face tangential stiffness parts.
+  std::vector<double> im_tc;          // 4 per entry: M_lo, M_hi, S_lo, S_hi
+  std::vector<double> irow_tdiag;     // 4 per interface row: their diagonals
 
   // Faces (canonical face layout) and their mass matrices.
   int nface = 0;
@@ -86,6 +95,7 @@ struct HostProblem {
   std::vector<int32_t> fm_ptr;        // face mass CSR over entries
   std::vector<int32_t> fm_col;        // global entry index
   std::vector<double> fm_val;
+  std::vector<double> fs_val;         // face tangential stiffness, same CSR
 
   // Copies of each node of the full grid (vector rows, subdomain order).
   std::vector<int32_t> cp_ptr;        // n_nodes + 1
@@ -131,9 +141,9 @@ struct DevSubState {
   int32_t* active;  // 1 while the subdomain's CG runs
   int32_t* iters;   // CG iterations of the current solve
   int32_t* status;  // 0 ok, 1 cap reached, 2 breakdown
-  unsigned* cnt_a;  // last-block counters, one set per kernel
-  unsigned* cnt_b;
-  unsigned* cnt_i;
+  float* sc;        // FP32 inner solve: power of two applied to both factors
+                    // of every FP32 dot product (keeps r*r out of underflow)
+  double* isc2;     // 1 / sc^2, undoes that scaling on the warp partials
 };
 
 // Loop-control block living in device memory.
@@ -164,11 +174,16 @@ struct DevProblem {
   // SELL
   const int64_t* slice_off;
   const int32_t* cols;
+  const uint16_t* cols16;     // 16-bit copy of cols (subdomains <= 65,536 padded rows), or null
+  int32_t c16_64, c16_32;     // 1: the FP64 / FP32 SpMVs read cols16 (chosen by the autotuner)
+  const int64_t* ub_tile0;    // first tile of each FP32-update block (kUpdGroup tiles, one subdomain)
+  int64_t n_ublocks;
   double* vals;
   const int32_t* tile_sub;
   const int64_t* sub_tile0;   // n_sub + 1
   int64_t n_tiles;
   int32_t n_sub;
+  int32_t rpl64, rpl32;       // SpMV variant (slices per warp) chosen by the autotuner
   // vectors (vec_rows each)
   double *x, *r, *z, *p, *q, *b, *f, *dinv, *w, *y;
   // per subdomain
@@ -180,12 +195,16 @@ struct DevProblem {
   int32_t n_irow;
   const int32_t *irow, *irow_sub, *ilam_ptr, *ilam, *im_ptr, *im_col;
   const double *irow_mdiag, *im_val, *im_kval;
+  const double *im_tc, *irow_tdiag;     // split face terms (HostProblem)
+  double* tc;                           // 4 per subdomain: p_lo, q_lo, p_hi, q_hi
+  double* im_t;                         // transmission part of each entry (set by k_set_robin)
   const int64_t* im_pos;
   const double* kdiag;
   // faces
   int64_t n_fent;
   const int32_t *fent_face, *fent_row_s, *fent_row_t, *fm_ptr, *fm_col;
   const double* fm_val;
+  const double* fs_val;
   const int32_t *face_s, *face_t, *face_n;
   const int64_t* face_eo;
   double* lam;
@@ -204,7 +223,6 @@ struct DevProblem {
   int32_t* inst_done;   // instance converged (or out of iterations) in this solve
   int32_t* inst_iters;  // Schwarz iterations of each instance
   double* inst_relres;  // last stop-test value of each instance
-  unsigned* inst_cnt;   // per-instance residual tickets
   // mixed precision (null in FP64 mode)
   float* vals32;
   const int64_t* im_pos32;
@@ -227,12 +245,22 @@ struct DevSample {
   double* lam;                          // [2 n_fent][kSampleWidth]
   double *part0, *part1, *part2;        // [n_tiles][kSampleWidth]
   double *rho, *alpha, *beta, *bb, *rr; // [n_sub][kSampleWidth]
+  float* sc;                            // [n_sub][kSampleWidth]: FP32 dot scale (power of two)
+  double* isc2;                         // [n_sub][kSampleWidth]: 1 / sc^2
   int32_t *active, *iters;              // [n_sub][kSampleWidth]
   int32_t* done;                        // [kSampleWidth]
   int32_t* outer_iters;                 // [kSampleWidth]
   double* relres;                       // [kSampleWidth]
   double *rpart, *rpart2;               // [kNodeBlocks][kSampleWidth]
   const int32_t* row_irow;              // [vec_rows]: interface-row index or -1
+  // mixed batch (null otherwise): FP32 correction e, r, z, p, q
+  float *x32, *r32, *z32, *pd32, *q32;  // [vec_rows][kSampleWidth]
+};
+
+// CG vectors of the batched evaluation in one precision.
+template <class T>
+struct MpVec {
+  T *x, *r, *z, *pd, *q;
 };
 
 // Adjoint gradient data (osm_adjoint.cu): device copies of the mesh and the
@@ -268,6 +296,10 @@ cudaError_t launch_rhs_gather(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_cg_init(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond,
                            int defect_norm = 0);
 cudaError_t launch_cg_iteration(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
+// The CG-step SpMV kernel alone (fp32: k_cg_spmv_dir32, else k_cg_spmv<double>)
+// and the state that makes it run on every subdomain (profiling only).
+cudaError_t launch_cg_spmv_alone(const DevProblem& d, int fp32, cudaStream_t s);
+cudaError_t launch_profile_state(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_cg_iteration32(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
 cudaError_t launch_cg_init_mixed(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
 cudaError_t launch_mixed_correct(const DevProblem& d, cudaStream_t s);
@@ -283,14 +315,21 @@ cudaError_t launch_stations_transpose(const DevProblem& d, const DevAdjoint& a, 
 cudaError_t launch_nodal_load(const DevProblem& d, const DevAdjoint& a, const double* v_nodes, cudaStream_t s);
 cudaError_t launch_density_gradient(const DevProblem& d, const DevAdjoint& a, const double* w_nodes, double* grad,
                                     cudaStream_t s);
+cudaError_t launch_nodal_split(const DevProblem& d, const double* v, double* out, cudaStream_t s);
+cudaError_t launch_exchange_adjoint(const DevProblem& d, const int32_t* partner, const double* lam, double* mu,
+                                    double p2, double* ub, cudaStream_t s);
+cudaError_t launch_dp_terms(const DevProblem& d, const double* lam, const double* u, const double* bbar, double* part,
+                            double* out, cudaStream_t s);
+cudaError_t launch_lambar_step(const DevProblem& d, const double* bbar, const double* lam_old, double* lam_new,
+                               cudaStream_t s);
 // batched p evaluation (osm_sample.cu)
 cudaError_t launch_mp_start(const DevProblem& d, const DevSample& m, cudaStream_t s);
 cudaError_t launch_mp_rhs_init(const DevProblem& d, const DevSample& m, cudaStream_t s, unsigned long long cond,
-                               int use_cond);
+                               int use_cond, int fp32, int refine);
 cudaError_t launch_mp_cg_iteration(const DevProblem& d, const DevSample& m, cudaStream_t s,
-                                   unsigned long long cond, int use_cond);
+                                   unsigned long long cond, int use_cond, int mixed);
 cudaError_t launch_mp_exchange_residual(const DevProblem& d, const DevSample& m, cudaStream_t s,
-                                        unsigned long long cond, int use_cond);
+                                        unsigned long long cond, int use_cond, int mixed);
 cudaError_t launch_residual(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
 cudaError_t launch_apply(const DevProblem& d, int op, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_gather_local(const DevProblem& d, const double* vec, double* canon, cudaStream_t s);

@@ -8,11 +8,11 @@
 // lane).  Every kernel therefore runs all subdomains, of any size, in one
 // launch; converged subdomains' tiles return at once.
 //
-// Reductions are deterministic: each tile writes its partial sums, and the
-// last tile of a subdomain to finish (atomic ticket) adds the subdomain's
-// partials in a fixed order and updates that subdomain's CG scalars.  Kernels
-// that steer a device-side loop do the same across the whole grid and call
-// cudaGraphSetConditional from that single last block.
+// Reductions are deterministic: each tile writes its partial sums, and a
+// small finaliser kernel (one warp per subdomain) adds a subdomain's partials
+// in a fixed order and updates that subdomain's CG scalars.  The finalisers
+// that steer a device-side loop take a last-block ticket across their few
+// blocks and call cudaGraphSetConditional from that single block.
 #include <cuda_runtime.h>
 
 #include "osm_device.cuh"
@@ -24,19 +24,28 @@ namespace {
 
 // ------------------------------------------------------------------ kernels
 
-// Robin matrix A_i = K_i + p_i M_Gi on interface rows, and its diagonal.
+// Transmission part of one interface entry: p_lo M_lo + p_hi M_hi + q_lo S_lo
+// + q_hi S_hi (c: the subdomain's p_lo, q_lo, p_hi, q_hi; t: the entry's
+// M_lo, M_hi, S_lo, S_hi).
+__device__ __forceinline__ double tc_term(const double* __restrict__ c, const double* __restrict__ t) {
+  return fma(c[0], t[0], fma(c[2], t[1], fma(c[1], t[2], c[3] * t[3])));
+}
+
+// Local matrix A_i = K_i + sum over faces (p M_G + q S_G) on interface rows
+// (Sec. 3; zeroth-order Robin: q = 0), and its diagonal.
 __global__ void k_set_robin(DevProblem d) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= d.n_irow) return;
-  const int s = d.irow_sub[k];
-  const double p = d.psub[s];
+  const double* c = d.tc + 4 * d.irow_sub[k];
   for (int32_t e = d.im_ptr[k]; e < d.im_ptr[k + 1]; ++e) {
-    const double a = d.im_kval[e] + p * d.im_val[e];
+    const double t = tc_term(c, d.im_tc + 4 * (int64_t)e);
+    const double a = d.im_kval[e] + t;
+    d.im_t[e] = t;
     d.vals[d.im_pos[e]] = a;
     if (d.vals32) d.vals32[d.im_pos32[e]] = (float)a;
   }
   const int32_t row = d.irow[k];
-  const double di = 1.0 / (d.kdiag[row] + p * d.irow_mdiag[k]);
+  const double di = 1.0 / (d.kdiag[row] + tc_term(c, d.irow_tdiag + 4 * (int64_t)k));
   d.dinv[row] = di;
   if (d.dinv32) d.dinv32[row] = (float)di;
 }
@@ -58,26 +67,29 @@ __global__ void k_rhs_gather(DevProblem d) {
 
 // CG start from the warm iterate x: r = b - A x, z = D^-1 r, p = z, and the
 // tile partials of ||r||^2, ||b||^2 and r.z (finalised by k_fin_init).
+template <int RPL, bool C16>
 __global__ void __launch_bounds__(kTileRows) k_cg_init(DevProblem d) {
   __shared__ double sm[3][kTileSlices];
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t slice = tile * kTileSlices + warp;
-  const int64_t off = d.slice_off[slice];
-  const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
   const int64_t t0 = d.sub_tile0[s];
-  const double* xs = d.x + t0 * kTileRows;
-  const int64_t row = tile * kTileRows + threadIdx.x;
-  const double ax = sell_row(d.cols, d.vals, off, w, lane, xs);
-  const double b = d.b[row];
-  const double r = b - ax;
-  const double z = d.dinv[row] * r;
-  d.r[row] = r;
-  d.z[row] = z;
-  d.p[row] = z;
-  double v[3] = {r * r, b * b, r * z};
-  block_sum<3>(v, sm);
+  double ax[RPL];
+  int64_t row[RPL];
+  tile_rows_any<double, RPL, C16>(d, d.vals, tile, d.x + t0 * kTileRows, ax, row);
+  double v[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) {
+    const double b = d.b[row[k]];
+    const double r = b - ax[k];
+    const double z = d.dinv[row[k]] * r;
+    d.r[row[k]] = r;
+    d.z[row[k]] = z;
+    d.p[row[k]] = z;
+    v[0] += r * r;
+    v[1] += b * b;
+    v[2] += r * z;
+  }
+  block_sum<3, kTileSlices / RPL>(v, sm);
   if (threadIdx.x == 0) {
     d.part0[tile] = v[0];
     d.part1[tile] = v[1];
@@ -85,25 +97,55 @@ __global__ void __launch_bounds__(kTileRows) k_cg_init(DevProblem d) {
   }
 }
 
+// Dot-product partial of one tile.  FP64 solve: FP64 products and sums.
+// FP32 inner solve: the warp adds FP32 products of the scaled factors
+// (x sc, y sc) and only the warp's sum is widened and unscaled (x isc2 =
+// 1/sc^2, exact); on this GPU FP64 arithmetic is scarce, and per-row FP64
+// sums made the short vector kernels ALU-bound.  Result in thread 0.
+template <class T, int NV, int NW>
+__device__ __forceinline__ void tile_dots(T (&v)[NV], double isc2, double (*sm)[kTileSlices], double (&out)[NV]) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    T t = v[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) sm[k][warp] = (double)t * isc2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) s += sm[k][w];
+      out[k] = s;
+    }
+  }
+}
+
 // q = A p and the tile partials of p.q on active subdomains (T = double for
-// the FP64 solve, float for the mixed-precision inner solve; dots in FP64).
-template <class T>
+// the FP64 solve, float for the mixed-precision inner solve).
+template <class T, int RPL, bool C16>
 __global__ void __launch_bounds__(kTileRows) k_cg_spmv(DevProblem d, CgVec<T> v) {
   __shared__ double sm[1][kTileSlices];
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
   if (!d.st.active[s]) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t slice = tile * kTileSlices + warp;
-  const int64_t off = d.slice_off[slice];
-  const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
   const int64_t t0 = d.sub_tile0[s];
-  const int64_t row = tile * kTileRows + threadIdx.x;
-  const T q = sell_row(d.cols, v.vals, off, w, lane, v.p + t0 * kTileRows);
-  v.q[row] = q;
-  double vv[1] = {(double)v.p[row] * (double)q};
-  block_sum<1>(vv, sm);
-  if (threadIdx.x == 0) d.part0[tile] = vv[0];
+  const T sc = sizeof(T) == 4 ? (T)d.st.sc[s] : T(1);
+  T q[RPL];
+  int64_t row[RPL];
+  tile_rows_any<T, RPL, C16>(d, v.vals, tile, v.p + t0 * kTileRows, q, row);
+  T vv[1] = {T(0)};
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) {
+    v.q[row[k]] = q[k];
+    vv[0] = fma(v.p[row[k]] * sc, q[k] * sc, vv[0]);
+  }
+  double out[1];
+  tile_dots<T, 1, kTileSlices / RPL>(vv, sizeof(T) == 4 ? d.st.isc2[s] : 1.0, sm, out);
+  if (threadIdx.x == 0) d.part0[tile] = out[0];
 }
 
 // x += alpha p, r -= alpha q, z = D^-1 r, and the tile partials of r.z and
@@ -113,22 +155,23 @@ __global__ void __launch_bounds__(kTileRows) k_cg_update(DevProblem d, CgVec<T> 
   __shared__ double sm[2][kTileSlices];
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
-  const int act = d.st.active[s];
-  if (act) {
-    const int64_t row = tile * kTileRows + threadIdx.x;
-    const T alpha = (T)d.st.alpha[s];
-    const T pr = v.p[row];
-    v.x[row] = fma(alpha, pr, v.x[row]);
-    const T r = fma(-alpha, v.q[row], v.r[row]);
-    const T z = v.dinv[row] * r;
-    v.r[row] = r;
-    v.z[row] = z;
-    double vv[2] = {(double)r * (double)z, (double)r * (double)r};
-    block_sum<2>(vv, sm);
-    if (threadIdx.x == 0) {
-      d.part1[tile] = vv[0];
-      d.part2[tile] = vv[1];
-    }
+  if (!d.st.active[s]) return;
+  const int64_t row = tile * kTileRows + threadIdx.x;
+  const T alpha = (T)d.st.alpha[s];
+  const T sc = sizeof(T) == 4 ? (T)d.st.sc[s] : T(1);
+  const T pr = v.p[row], xr = v.x[row], qr = v.q[row], rr0 = v.r[row], di = v.dinv[row];
+  v.x[row] = fma(alpha, pr, xr);
+  const T r = fma(-alpha, qr, rr0);
+  const T z = di * r;
+  v.r[row] = r;
+  v.z[row] = z;
+  const T rs = r * sc;
+  T vv[2] = {rs * (z * sc), rs * rs};
+  double out[2];
+  tile_dots<T, 2, kTileSlices>(vv, sizeof(T) == 4 ? d.st.isc2[s] : 1.0, sm, out);
+  if (threadIdx.x == 0) {
+    d.part1[tile] = out[0];
+    d.part2[tile] = out[1];
   }
 }
 
@@ -145,6 +188,9 @@ __global__ void k_fin_init(DevProblem d, int mixed, unsigned long long cond, int
   __shared__ bool flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.x * kTileSlices + warp;
+  // a graph that runs the subdomain solves alone (no k_rhs_gather) starts the
+  // wall clock here; the ticket's fence publishes it to the last block
+  if (blockIdx.x == 0 && threadIdx.x == 0 && d.ctl->t_start_ns == 0ull) d.ctl->t_start_ns = global_ns();
   if (s < d.n_sub) {
     const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
     const double a0 = warp_sum_parts(d.part0, t0, nt);
@@ -157,6 +203,15 @@ __global__ void k_fin_init(DevProblem d, int mixed, unsigned long long cond, int
       d.st.beta[s] = 0.0;
       d.st.iters[s] = 0;
       d.st.status[s] = 0;
+      // scale of the FP32 dot products: sc = 2^-e with 2^e ~ rms of the defect
+      int e = 0;
+      const double ms = a0 / (double)(nt * kTileRows);
+      if (mixed && ms > 0.0 && isfinite(ms)) {
+        frexp(sqrt(ms), &e);
+        e = max(-120, min(120, e));
+      }
+      d.st.sc[s] = (float)ldexp(1.0, -e);
+      d.st.isc2[s] = ldexp(1.0, 2 * e);
       const int act = !d.inst_done[d.sub_inst[s]] &&
                       (mixed ? (!(a0 <= d.ctl->tau2_outer * a1) && a2 > 0.0) : !(a0 <= d.ctl->tau2 * a1));
       d.st.active[s] = act;
@@ -191,7 +246,9 @@ __global__ void k_fin_alpha(DevProblem d) {
 
 // rho = r.z, the stop test ||r|| <= tau ||b|| (or the iteration cap), beta;
 // the last block counts the step and sets the inner loop condition.
-__global__ void k_fin_beta(DevProblem d, unsigned long long cond, int use_cond) {
+// check_pq (three-kernel FP32 step, no k_fin_alpha): a subdomain whose p.q
+// partials (still in part0) sum to <= 0 stops with a breakdown.
+__global__ void k_fin_beta(DevProblem d, unsigned long long cond, int use_cond, int check_pq) {
   __shared__ bool flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.x * kTileSlices + warp;
@@ -199,11 +256,17 @@ __global__ void k_fin_beta(DevProblem d, unsigned long long cond, int use_cond) 
     const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
     const double rz = warp_sum_parts(d.part1, t0, nt);
     const double rr = warp_sum_parts(d.part2, t0, nt);
+    const double pq = check_pq ? warp_sum_parts(d.part0, t0, nt) : 1.0;
     if (lane == 0) {
       const int it = d.st.iters[s] + 1;
       d.st.iters[s] = it;
       d.st.rr[s] = rr;
-      if (rr <= d.ctl->tau2 * d.st.bb[s]) {
+      if (!(pq > 0.0) || !isfinite(pq)) {
+        d.st.status[s] |= 2;
+        atomicOr(&d.ctl->status, 2);
+        d.st.active[s] = 0;
+        atomicSub(&d.ctl->n_active, 1);
+      } else if (rr <= d.ctl->tau2 * d.st.bb[s]) {
         d.st.active[s] = 0;
         atomicSub(&d.ctl->n_active, 1);
       } else if (it >= d.ctl->max_inner) {
@@ -235,32 +298,152 @@ __global__ void __launch_bounds__(kTileRows) k_cg_direction(DevProblem d, CgVec<
   v.p[row] = fma((T)d.st.beta[s], v.p[row], v.z[row]);
 }
 
+// FP32 inner CG of the mixed form in three kernels per step.  With
+// t = A z, the direction update moves into the SpMV's epilogue:
+//   p = z + beta p,   q = A p = t + beta q   (first step, beta = 0: p = z, q = t)
+// and alpha = rho / (p.q) is formed inside the update kernel (every block
+// of a subdomain adds the subdomain's p.q partials in the same fixed order),
+// so k_cg_direction and k_fin_alpha drop out.  Same vector traffic as the
+// five-kernel step, two launches and one pass over the vectors fewer.
+template <int RPL, bool C16>
+__global__ void __launch_bounds__(kTileRows) k_cg_spmv_dir32(DevProblem d) {
+  __shared__ double sm[1][kTileSlices];
+  const int64_t tile = blockIdx.x;
+  const int s = d.tile_sub[tile];
+  if (!d.st.active[s]) return;
+  const int64_t t0 = d.sub_tile0[s];
+  const double beta64 = d.st.beta[s];
+  const bool first = beta64 == 0.0;   // uniform per subdomain: no read of p, q
+  const float beta = (float)beta64, sc = d.st.sc[s];
+  float t[RPL];
+  int64_t row[RPL];
+  tile_rows_any<float, RPL, C16>(d, d.vals32, tile, d.z32 + t0 * kTileRows, t, row);
+  float vv[1] = {0.f};
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) {
+    const float z = d.z32[row[k]];
+    float p = z, q = t[k];
+    if (!first) {
+      p = fmaf(beta, d.p32[row[k]], z);
+      q = fmaf(beta, d.q32[row[k]], t[k]);
+    }
+    d.p32[row[k]] = p;
+    d.q32[row[k]] = q;
+    vv[0] = fmaf(p * sc, q * sc, vv[0]);
+  }
+  double out[1];
+  tile_dots<float, 1, kTileSlices / RPL>(vv, d.st.isc2[s], sm, out);
+  if (threadIdx.x == 0) d.part0[tile] = out[0];
+}
+
+// alpha = rho / (p.q) (a breakdown, p.q <= 0, leaves the iterate alone and
+// k_fin_beta stops the subdomain), x += alpha p, r -= alpha q, z = D^-1 r,
+// and the tile partials of r.z and ||r||^2.  A block covers up to
+// kUpdGroup consecutive tiles of one subdomain (d.ub_tile0): alpha is formed
+// once per block, and every thread issues the loads of all its rows before
+// it waits for alpha, so the launch is about one wave of long-lived blocks
+// instead of many waves of blocks that each wait on alpha's L2 round trips.
+__global__ void __launch_bounds__(kTileRows) k_cg_update_a32(DevProblem d) {
+  __shared__ double sm[kUpdGroup][2][kTileSlices];
+  __shared__ float s_alpha;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t t0 = d.ub_tile0[blockIdx.x];
+  const int s = d.tile_sub[t0];
+  if (!d.st.active[s]) return;
+  const int64_t ts0 = d.sub_tile0[s];
+  const int nt = (int)min((int64_t)kUpdGroup, d.sub_tile0[s + 1] - t0);
+  float pr[kUpdGroup], xr[kUpdGroup], qr[kUpdGroup], rr0[kUpdGroup], di[kUpdGroup];
+#pragma unroll
+  for (int j = 0; j < kUpdGroup; ++j) {
+    if (j < nt) {
+      const int64_t row = (t0 + j) * kTileRows + threadIdx.x;
+      pr[j] = d.p32[row];
+      xr[j] = d.x32[row];
+      qr[j] = d.q32[row];
+      rr0[j] = d.r32[row];
+      di[j] = d.dinv32[row];
+    }
+  }
+  if (warp == 0) {
+    const double pq = warp_sum_parts(d.part0, ts0, d.sub_tile0[s + 1] - ts0);
+    if (lane == 0) s_alpha = (pq > 0.0 && isfinite(pq)) ? (float)(d.st.rho[s] / pq) : 0.f;
+  }
+  __syncthreads();
+  const float alpha = s_alpha, sc = d.st.sc[s];
+  const double isc2 = d.st.isc2[s];
+#pragma unroll
+  for (int j = 0; j < kUpdGroup; ++j) {
+    float a = 0.f, b = 0.f;
+    if (j < nt) {
+      const int64_t row = (t0 + j) * kTileRows + threadIdx.x;
+      d.x32[row] = fmaf(alpha, pr[j], xr[j]);
+      const float r = fmaf(-alpha, qr[j], rr0[j]);
+      const float z = di[j] * r;
+      d.r32[row] = r;
+      d.z32[row] = z;
+      const float rs = r * sc;
+      a = rs * (z * sc);
+      b = rs * rs;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      sm[j][0][warp] = (double)a * isc2;
+      sm[j][1][warp] = (double)b * isc2;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * nt) {
+    const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
+    double v = 0.0;
+#pragma unroll
+    for (int w = 0; w < kTileSlices; ++w) v += sm[j][which][w];
+    (which ? d.part2 : d.part1)[t0 + j] = v;
+  }
+}
+
+// Profiling state: every subdomain active, beta = 1/2 (the full epilogue of
+// k_cg_spmv_dir32 runs), unit dot scale.
+__global__ void k_profile_state(DevProblem d) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= d.n_sub) return;
+  d.st.active[s] = 1;
+  d.st.beta[s] = 0.5;
+  d.st.sc[s] = 1.f;
+  d.st.isc2[s] = 1.0;
+}
+
 // Mixed precision, start of one refinement step: FP64 defect
 // d = b - A u (FP64 values and accumulation), then the FP32 CG on A e = d
-// from e = 0: r = d, z = D^-1 r, p = z.  A subdomain whose FP64 defect already
-// meets the FP64 tolerance (||d|| <= inner_rtol ||b||) is not corrected; the
-// FP32 solve stops at ||r|| <= mixed_inner_rtol ||d||.
+// from e = 0: r = d, z = D^-1 r, p = z, and the tile partials of ||d||^2,
+// ||b||^2 and r.z (k_fin_init decides which subdomains are corrected).
+template <int RPL, bool C16>
 __global__ void __launch_bounds__(kTileRows) k_cg_init_mixed(DevProblem d) {
   __shared__ double sm[3][kTileSlices];
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t slice = tile * kTileSlices + warp;
-  const int64_t off = d.slice_off[slice];
-  const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
   const int64_t t0 = d.sub_tile0[s];
-  const int64_t row = tile * kTileRows + threadIdx.x;
-  const double ax = sell_row(d.cols, d.vals, off, w, lane, d.x + t0 * kTileRows);
-  const double b = d.b[row];
-  const double dfc = b - ax;
-  const float r = (float)dfc;
-  const float z = d.dinv32[row] * r;
-  d.r32[row] = r;
-  d.z32[row] = z;
-  d.p32[row] = z;
-  d.x32[row] = 0.f;
-  double vv[3] = {dfc * dfc, b * b, (double)r * (double)z};
-  block_sum<3>(vv, sm);
+  double ax[RPL];
+  int64_t row[RPL];
+  tile_rows_any<double, RPL, C16>(d, d.vals, tile, d.x + t0 * kTileRows, ax, row);
+  double vv[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) {
+    const double b = d.b[row[k]];
+    const double dfc = b - ax[k];
+    const float r = (float)dfc;
+    const float z = d.dinv32[row[k]] * r;
+    d.r32[row[k]] = r;
+    d.z32[row[k]] = z;   // p = z is formed by the first k_cg_spmv_dir32 (beta = 0)
+    d.x32[row[k]] = 0.f;
+    vv[0] += dfc * dfc;
+    vv[1] += b * b;
+    vv[2] += (double)r * (double)z;
+  }
+  block_sum<3, kTileSlices / RPL>(vv, sm);
   if (threadIdx.x == 0) {
     d.part0[tile] = vv[0];
     d.part1[tile] = vv[1];
@@ -275,16 +458,16 @@ __global__ void __launch_bounds__(kTileRows) k_mixed_correct(DevProblem d) {
 }
 
 // y32 = A32 x32 (FP32 values) on every tile: the mixed inner operator.
+template <int RPL, bool C16>
 __global__ void __launch_bounds__(kTileRows) k_spmv_plain32(DevProblem d, const float* __restrict__ x,
                                                             float* __restrict__ y) {
   const int64_t tile = blockIdx.x;
-  const int s = d.tile_sub[tile];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t slice = tile * kTileSlices + warp;
-  const int64_t off = d.slice_off[slice];
-  const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
-  const int64_t t0 = d.sub_tile0[s];
-  y[tile * kTileRows + threadIdx.x] = sell_row(d.cols, d.vals32, off, w, lane, x + t0 * kTileRows);
+  const int64_t t0 = d.sub_tile0[d.tile_sub[tile]];
+  float q[RPL];
+  int64_t row[RPL];
+  tile_rows_any<float, RPL, C16>(d, d.vals32, tile, x + t0 * kTileRows, q, row);
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) y[row[k]] = q[k];
 }
 
 __global__ void k_scatter_local32(DevProblem d, const double* __restrict__ canon, float* __restrict__ vec) {
@@ -309,19 +492,37 @@ __global__ void k_exchange(DevProblem d) {
   const int64_t eo = d.face_eo[f];
   const int32_t nf = d.face_n[f];
   const int64_t m = e - eo;
-  double mus = 0.0, mut = 0.0;
-  for (int32_t k = d.fm_ptr[e]; k < d.fm_ptr[e + 1]; ++k) {
-    const double mv = d.fm_val[k];
-    const int32_t c = d.fm_col[k];
-    mus = fma(mv, d.x[d.fent_row_s[c]], mus);
-    mut = fma(mv, d.x[d.fent_row_t[c]], mut);
+  // s is the lower side of the face: its (p_lo, q_lo) plus t's (p_hi, q_hi)
+  const double* cs = d.tc + 4 * d.face_s[f];
+  const double* ct = d.tc + 4 * d.face_t[f];
+  const double pp = cs[0] + ct[2], qq = cs[1] + ct[3];
+  double mus = 0.0, mut = 0.0, sus = 0.0, sut = 0.0;
+  const int32_t k0 = d.fm_ptr[e], k1 = d.fm_ptr[e + 1];
+  if (qq == 0.0) {   // zeroth-order Robin: the face mass only
+#pragma unroll 4
+    for (int32_t k = k0; k < k1; ++k) {
+      const double mv = d.fm_val[k];
+      const int32_t c = d.fm_col[k];
+      mus = fma(mv, d.x[d.fent_row_s[c]], mus);
+      mut = fma(mv, d.x[d.fent_row_t[c]], mut);
+    }
+  } else {
+#pragma unroll 4
+    for (int32_t k = k0; k < k1; ++k) {
+      const double mv = d.fm_val[k], sv = d.fs_val[k];
+      const int32_t c = d.fm_col[k];
+      const double xs = d.x[d.fent_row_s[c]], xt = d.x[d.fent_row_t[c]];
+      mus = fma(mv, xs, mus);
+      mut = fma(mv, xt, mut);
+      sus = fma(sv, xs, sus);
+      sut = fma(sv, xt, sut);
+    }
   }
-  const double pp = d.psub[d.face_s[f]] + d.psub[d.face_t[f]];
   double* lst = d.lam + 2 * eo + m;
   double* lts = d.lam + 2 * eo + nf + m;
   const double old_st = *lst, old_ts = *lts;
-  *lst = pp * mut - old_ts;
-  *lts = pp * mus - old_st;
+  *lst = fma(pp, mut, qq * sut) - old_ts;
+  *lts = fma(pp, mus, qq * sus) - old_st;
 }
 
 // Stop test, step 1: ubar = average of the copies of each node; phi = ubar
@@ -337,49 +538,43 @@ __global__ void k_average(DevProblem d) {
     }
     double s = 0.0;
     for (int32_t c = c0; c < c1; ++c) s += d.x[d.cp_idx[c]];
-    const double ub = s / (double)(c1 - c0);
+    const double ub = copy_mean(s, c1 - c0);
     d.phi[n] = ub;
     for (int32_t c = c0; c < c1; ++c) d.w[d.cp_idx[c]] = ub;
   }
 }
 
 // y = A x on every tile (all subdomains).
+template <int RPL, bool C16>
 __global__ void __launch_bounds__(kTileRows) k_spmv_plain(DevProblem d, const double* __restrict__ x,
                                                           double* __restrict__ y) {
   const int64_t tile = blockIdx.x;
-  const int s = d.tile_sub[tile];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t slice = tile * kTileSlices + warp;
-  const int64_t off = d.slice_off[slice];
-  const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
-  const int64_t t0 = d.sub_tile0[s];
-  y[tile * kTileRows + threadIdx.x] = sell_row(d.cols, d.vals, off, w, lane, x + t0 * kTileRows);
+  const int64_t t0 = d.sub_tile0[d.tile_sub[tile]];
+  double q[RPL];
+  int64_t row[RPL];
+  tile_rows_any<double, RPL, C16>(d, d.vals, tile, x + t0 * kTileRows, q, row);
+#pragma unroll
+  for (int k = 0; k < RPL; ++k) y[row[k]] = q[k];
 }
 
-// y -= p_i M_Gi x on interface rows: turns A_i x into K_i x.
+// y -= (transmission part of A_i) x on interface rows: turns A_i x into K_i x.
 __global__ void k_face_correct(DevProblem d, const double* __restrict__ x, double* __restrict__ y) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= d.n_irow) return;
-  const double p = d.psub[d.irow_sub[k]];
   double acc = 0.0;
-  for (int32_t e = d.im_ptr[k]; e < d.im_ptr[k + 1]; ++e) acc = fma(d.im_val[e], x[d.im_col[e]], acc);
+  for (int32_t e = d.im_ptr[k]; e < d.im_ptr[k + 1]; ++e) acc = fma(d.im_t[e], x[d.im_col[e]], acc);
   const int32_t row = d.irow[k];
-  y[row] -= p * acc;
+  y[row] -= acc;
 }
 
-// Stop test, step 2: r = sum_copies f - sum_copies K_i ubar per node and
-// ||r|| / ||f|| per instance by a deterministic two-level sum.  The last
-// block of an instance records its residual and whether it is done (reached
-// rtol or max_outer); the last block overall counts the Schwarz iteration
-// and sets the outer loop condition (any instance still running).
-__global__ void __launch_bounds__(256) k_residual(DevProblem d, unsigned long long cond, int use_cond) {
+// Stop test, step 2: r = sum_copies f - sum_copies K_i ubar per node, and
+// the per-block partials of ||r||^2 and ||f||^2 (no tickets: the single-block
+// k_residual_fin adds them).
+__global__ void __launch_bounds__(256) k_residual(DevProblem d) {
   __shared__ double sm[2][kTileSlices];
-  __shared__ bool flag;
   const int b = blockIdx.x;
-  const int inst = d.rblock_inst[b];
-  const bool live = !d.inst_done[inst];
   double v[2] = {0.0, 0.0};
-  if (live) {
+  if (!d.inst_done[d.rblock_inst[b]]) {
     for (int64_t n = d.rblock_node0[b] + threadIdx.x; n < d.rblock_node0[b + 1]; n += blockDim.x) {
       const int32_t c0 = d.cp_ptr[n], c1 = d.cp_ptr[n + 1];
       double fg = 0.0, ku = 0.0;
@@ -397,17 +592,35 @@ __global__ void __launch_bounds__(256) k_residual(DevProblem d, unsigned long lo
     d.rpart[b] = v[0];
     d.rpart2[b] = v[1];
   }
-  const int b0 = d.inst_rblock0[inst], nb = d.inst_rblock0[inst + 1] - b0;
-  if (last_block(&d.inst_cnt[inst], (unsigned)nb, &flag) && live) {
-    double u[2] = {0.0, 0.0};
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+}
+
+// Stop test, step 3 (one block): per instance, ||r|| / ||f|| from its block
+// partials in a fixed order, its iteration count and whether it is done
+// (reached rtol or max_outer); then counts the Schwarz iteration and sets
+// the outer loop condition (any instance still running).
+__global__ void __launch_bounds__(kResFinThreads) k_residual_fin(DevProblem d, unsigned long long cond, int use_cond) {
+  __shared__ double sm[2][kResFinThreads / 32];
+  const int n_outer = d.ctl->n_outer;
+  for (int inst = 0; inst < d.n_inst; ++inst) {
+    if (d.inst_done[inst]) continue;   // uniform across the block
+    const int b0 = d.inst_rblock0[inst], nb = d.inst_rblock0[inst + 1] - b0;
+    double u[2] = {0.0, 0.0}, w[2] = {0.0, 0.0};
+    int k = threadIdx.x;
+    for (; k + (int)blockDim.x < nb; k += 2 * blockDim.x) {
+      u[0] += __ldcg(d.rpart + b0 + k);
+      u[1] += __ldcg(d.rpart2 + b0 + k);
+      w[0] += __ldcg(d.rpart + b0 + k + blockDim.x);
+      w[1] += __ldcg(d.rpart2 + b0 + k + blockDim.x);
+    }
+    if (k < nb) {
       u[0] += __ldcg(d.rpart + b0 + k);
       u[1] += __ldcg(d.rpart2 + b0 + k);
     }
-    block_sum<2>(u, sm);
+    u[0] += w[0];
+    u[1] += w[1];
+    block_sum<2, kResFinThreads / 32>(u, sm);
     if (threadIdx.x == 0) {
       const double rel = u[1] > 0.0 ? sqrt(u[0] / u[1]) : sqrt(u[0]);
-      const int n_outer = d.ctl->n_outer;
       d.inst_relres[inst] = rel;
       d.inst_iters[inst] = n_outer + 1;
       if (d.n_inst == 1) {
@@ -416,9 +629,10 @@ __global__ void __launch_bounds__(256) k_residual(DevProblem d, unsigned long lo
       }
       if (!(rel > d.ctl->rtol) || !isfinite(rel) || n_outer + 1 >= d.ctl->max_outer) d.inst_done[inst] = 1;
     }
+    __syncthreads();   // sm is reused by the next instance
   }
-  if (last_block(&d.ctl->gcnt_r, gridDim.x, &flag) && threadIdx.x == 0) {
-    d.ctl->n_outer += 1;
+  if (threadIdx.x == 0) {
+    d.ctl->n_outer = n_outer + 1;
     int running = 0;
     double worst = 0.0;
     for (int i = 0; i < d.n_inst; ++i) {
@@ -447,6 +661,20 @@ __global__ void k_gather_local(DevProblem d, const double* __restrict__ vec, dou
 inline unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 inline unsigned fin_blocks(const DevProblem& d) { return (unsigned)((d.n_sub + kTileSlices - 1) / kTileSlices); }
 
+// Launch an SpMV-bearing kernel in the variant chosen at setup by the
+// autotuner: RPL slices per warp (256 / RPL threads per 256-row tile) and
+// 16- or 32-bit column indices (c16).
+#define OSM_LAUNCH_RPL(rpl, c16, KERNEL, s, ...)                                                  \
+  do {                                                                                            \
+    if (c16) {                                                                                    \
+      if ((rpl) == 2) KERNEL<2, true><<<(unsigned)d.n_tiles, kTileRows / 2, 0, s>>>(__VA_ARGS__); \
+      else KERNEL<1, true><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(__VA_ARGS__);                \
+    } else {                                                                                      \
+      if ((rpl) == 2) KERNEL<2, false><<<(unsigned)d.n_tiles, kTileRows / 2, 0, s>>>(__VA_ARGS__); \
+      else KERNEL<1, false><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(__VA_ARGS__);                \
+    }                                                                                             \
+  } while (0)
+
 }  // namespace
 
 cudaError_t launch_set_robin(const DevProblem& d, cudaStream_t s) {
@@ -462,33 +690,57 @@ cudaError_t launch_rhs_gather(const DevProblem& d, cudaStream_t s) {
 
 cudaError_t launch_cg_init(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond,
                            int defect_norm) {
-  k_cg_init<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d);
+  OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_cg_init, s, d);
   k_fin_init<<<fin_blocks(d), kTileRows, 0, s>>>(d, defect_norm, cond, use_cond);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_iteration(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
   const CgVec<double> v{d.x, d.r, d.z, d.p, d.q, d.dinv, d.vals};
-  k_cg_spmv<double><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
+  if (d.c16_64) {
+    if (d.rpl64 == 2) k_cg_spmv<double, 2, true><<<(unsigned)d.n_tiles, kTileRows / 2, 0, s>>>(d, v);
+    else k_cg_spmv<double, 1, true><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
+  } else {
+    if (d.rpl64 == 2) k_cg_spmv<double, 2, false><<<(unsigned)d.n_tiles, kTileRows / 2, 0, s>>>(d, v);
+    else k_cg_spmv<double, 1, false><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
+  }
   k_fin_alpha<<<fin_blocks(d), kTileRows, 0, s>>>(d);
   k_cg_update<double><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
-  k_fin_beta<<<fin_blocks(d), kTileRows, 0, s>>>(d, cond, use_cond);
+  k_fin_beta<<<fin_blocks(d), kTileRows, 0, s>>>(d, cond, use_cond, 0);
   k_cg_direction<double><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_iteration32(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
-  const CgVec<float> v{d.x32, d.r32, d.z32, d.p32, d.q32, d.dinv32, d.vals32};
-  k_cg_spmv<float><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
-  k_fin_alpha<<<fin_blocks(d), kTileRows, 0, s>>>(d);
-  k_cg_update<float><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
-  k_fin_beta<<<fin_blocks(d), kTileRows, 0, s>>>(d, cond, use_cond);
-  k_cg_direction<float><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
+  OSM_LAUNCH_RPL(d.rpl32, d.c16_32, k_cg_spmv_dir32, s, d);
+  k_cg_update_a32<<<(unsigned)d.n_ublocks, kTileRows, 0, s>>>(d);
+  k_fin_beta<<<fin_blocks(d), kTileRows, 0, s>>>(d, cond, use_cond, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_spmv_alone(const DevProblem& d, int fp32, cudaStream_t s) {
+  if (fp32) {
+    OSM_LAUNCH_RPL(d.rpl32, d.c16_32, k_cg_spmv_dir32, s, d);
+  } else {
+    const CgVec<double> v{d.x, d.r, d.z, d.p, d.q, d.dinv, d.vals};
+    if (d.c16_64) {
+      if (d.rpl64 == 2) k_cg_spmv<double, 2, true><<<(unsigned)d.n_tiles, kTileRows / 2, 0, s>>>(d, v);
+      else k_cg_spmv<double, 1, true><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
+    } else {
+      if (d.rpl64 == 2) k_cg_spmv<double, 2, false><<<(unsigned)d.n_tiles, kTileRows / 2, 0, s>>>(d, v);
+      else k_cg_spmv<double, 1, false><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_profile_state(const DevProblem& d, cudaStream_t s) {
+  k_profile_state<<<blocks_for(d.n_sub, 256), 256, 0, s>>>(d);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_init_mixed(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
-  k_cg_init_mixed<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d);
+  OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_cg_init_mixed, s, d);
   k_fin_init<<<fin_blocks(d), kTileRows, 0, s>>>(d, 1, cond, use_cond);
   return cudaGetLastError();
 }
@@ -499,13 +751,13 @@ cudaError_t launch_mixed_correct(const DevProblem& d, cudaStream_t s) {
 }
 
 cudaError_t launch_spmv_plain32(const DevProblem& d, const float* x, float* y, cudaStream_t s) {
-  k_spmv_plain32<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, x, y);
+  OSM_LAUNCH_RPL(d.rpl32, d.c16_32, k_spmv_plain32, s, d, x, y);
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply32(const DevProblem& d, const double* x, double* y, cudaStream_t s) {
   k_scatter_local32<<<blocks_for(d.n_local, 256), 256, 0, s>>>(d, x, d.z32);
-  k_spmv_plain32<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, d.z32, d.q32);
+  OSM_LAUNCH_RPL(d.rpl32, d.c16_32, k_spmv_plain32, s, d, d.z32, d.q32);
   k_gather_local32<<<blocks_for(d.n_local, 256), 256, 0, s>>>(d, d.q32, y);
   return cudaGetLastError();
 }
@@ -517,21 +769,22 @@ cudaError_t launch_exchange(const DevProblem& d, cudaStream_t s) {
 }
 
 cudaError_t launch_spmv_plain(const DevProblem& d, const double* x, double* y, cudaStream_t s) {
-  k_spmv_plain<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, x, y);
+  OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_spmv_plain, s, d, x, y);
   return cudaGetLastError();
 }
 
 cudaError_t launch_residual(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
   k_average<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
-  k_spmv_plain<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, d.w, d.y);
+  OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_spmv_plain, s, d, d.w, d.y);
   if (d.n_irow) k_face_correct<<<blocks_for(d.n_irow, 256), 256, 0, s>>>(d, d.w, d.y);
-  k_residual<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d, cond, use_cond);
+  k_residual<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
+  k_residual_fin<<<1, kResFinThreads, 0, s>>>(d, cond, use_cond);
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply(const DevProblem& d, int op, const double* x, double* y, cudaStream_t s) {
   k_scatter_local<<<blocks_for(d.n_local, 256), 256, 0, s>>>(d, x, d.w);
-  k_spmv_plain<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, d.w, d.y);
+  OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_spmv_plain, s, d, d.w, d.y);
   if (op == 1 && d.n_irow) k_face_correct<<<blocks_for(d.n_irow, 256), 256, 0, s>>>(d, d.w, d.y);
   k_gather_local<<<blocks_for(d.n_local, 256), 256, 0, s>>>(d, d.y, y);
   return cudaGetLastError();
@@ -540,7 +793,7 @@ cudaError_t launch_apply(const DevProblem& d, int op, const double* x, double* y
 cudaError_t launch_apply_scratch(const DevProblem& d, int op, const double* x, double* y, double* w_scratch,
                                  double* y_scratch, cudaStream_t s) {
   k_scatter_local<<<blocks_for(d.n_local, 256), 256, 0, s>>>(d, x, w_scratch);
-  k_spmv_plain<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, w_scratch, y_scratch);
+  OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_spmv_plain, s, d, w_scratch, y_scratch);
   if (op == 1 && d.n_irow) k_face_correct<<<blocks_for(d.n_irow, 256), 256, 0, s>>>(d, w_scratch, y_scratch);
   k_gather_local<<<blocks_for(d.n_local, 256), 256, 0, s>>>(d, y_scratch, y);
   return cudaGetLastError();

@@ -52,42 +52,64 @@ __device__ __forceinline__ double lane_sum_tiles(const double* part, int64_t t0,
 
 // Row `row` (slice lane `rl` of the slice at `off`, width w) times the
 // candidates' vectors: lane k returns (K x_k)[row] (+ p_k (M_G x_k)[row]
-// when `robin`).  Xs: subdomain base of X, Xg: X itself.
-__device__ __forceinline__ double mp_row(const DevProblem& d, const DevSample& m, int64_t off, int rl, int w,
-                                         const double* __restrict__ Xs, const double* __restrict__ Xg,
-                                         int64_t row, bool robin, double pk, int k) {
+// when `robin`).  Xs: subdomain base of X, Xg: X itself.  FP64 reads the
+// FP64 values (pair layout), FP32 the FP32 values (quad layout).
+template <class T>
+__device__ __forceinline__ T mp_row(const DevProblem& d, const DevSample& m, int64_t off, int rl, int w,
+                                    const T* __restrict__ Xs, const T* __restrict__ Xg, int64_t row, bool robin,
+                                    double pk, int k) {
   const int4* c4 = reinterpret_cast<const int4*>(d.cols + off) + rl;
-  const double2* v2 = reinterpret_cast<const double2*>(d.vals + off) + rl;
-  double acc0 = 0.0, acc1 = 0.0;
+  T acc0 = T(0), acc1 = T(0);
   const int nq = w >> 2;
 #pragma unroll 2
   for (int q = 0; q < nq; ++q) {
     const int4 c = __ldg(c4 + q * 32);
-    const double2 a = __ldg(v2 + q * 64);
-    const double2 b = __ldg(v2 + q * 64 + 32);
-    acc0 = fma(a.x, Xs[(int64_t)c.x * W + k], acc0);
-    acc1 = fma(a.y, Xs[(int64_t)c.y * W + k], acc1);
-    acc0 = fma(b.x, Xs[(int64_t)c.z * W + k], acc0);
-    acc1 = fma(b.y, Xs[(int64_t)c.w * W + k], acc1);
+    if constexpr (sizeof(T) == 8) {
+      const double2* v2 = reinterpret_cast<const double2*>(d.vals + off) + rl;
+      const double2 a = __ldg(v2 + q * 64);
+      const double2 b = __ldg(v2 + q * 64 + 32);
+      acc0 = fma(a.x, Xs[(int64_t)c.x * W + k], acc0);
+      acc1 = fma(a.y, Xs[(int64_t)c.y * W + k], acc1);
+      acc0 = fma(b.x, Xs[(int64_t)c.z * W + k], acc0);
+      acc1 = fma(b.y, Xs[(int64_t)c.w * W + k], acc1);
+    } else {
+      const float4 a = __ldg(reinterpret_cast<const float4*>(d.vals32 + off) + rl + q * 32);
+      acc0 = fmaf(a.x, Xs[(int64_t)c.x * W + k], acc0);
+      acc1 = fmaf(a.y, Xs[(int64_t)c.y * W + k], acc1);
+      acc0 = fmaf(a.z, Xs[(int64_t)c.z * W + k], acc0);
+      acc1 = fmaf(a.w, Xs[(int64_t)c.w * W + k], acc1);
+    }
   }
-  double acc = acc0 + acc1;
+  T acc = acc0 + acc1;
   if (robin) {
     const int32_t ir = m.row_irow[row];
     if (ir >= 0) {
-      double f = 0.0;
-      for (int32_t e = d.im_ptr[ir]; e < d.im_ptr[ir + 1]; ++e) f = fma(d.im_val[e], Xg[(int64_t)d.im_col[e] * W + k], f);
-      acc = fma(pk, f, acc);
+      T f = T(0);
+      for (int32_t e = d.im_ptr[ir]; e < d.im_ptr[ir + 1]; ++e)
+        f = fma((T)d.im_val[e], Xg[(int64_t)d.im_col[e] * W + k], f);
+      acc = fma((T)pk, f, acc);
     }
   }
   return acc;
 }
 
+// Jacobi scale of candidate k on `row`: 1 / (diag K + p_k diag M_G).  Off
+// the interface it is the stored 1 / diag K (padding rows: 0), one broadcast
+// load; only interface rows divide (FP64 division is slow on this GPU).
 __device__ __forceinline__ double mp_dinv(const DevProblem& d, const DevSample& m, int64_t row, double pk) {
-  const double kd = d.kdiag[row];
-  if (kd == 0.0) return 0.0;  // padding row
   const int32_t ir = m.row_irow[row];
-  return 1.0 / (kd + (ir >= 0 ? pk * d.irow_mdiag[ir] : 0.0));
+  if (ir < 0) return d.dinv[row];
+  return 1.0 / (d.kdiag[row] + pk * d.irow_mdiag[ir]);
 }
+
+// Dot-product term of the FP32 inner solve: products of the factors scaled
+// by sc (a power of two per subdomain and candidate, set from the defect) are
+// summed in FP32 over the slice's rows; the caller widens and unscales once.
+template <class T>
+struct MpDot {
+  T acc = T(0);
+  __device__ __forceinline__ void add(T a, T b, T sc) { acc = fma(a * sc, b * sc, acc); }
+};
 
 // b_k = f on every row, for every candidate (start of a batched run).
 __global__ void k_mp_bcast_f(DevProblem d, DevSample m, int64_t n) {
@@ -127,7 +149,7 @@ __global__ void __launch_bounds__(kTileRows) k_mp_cg_init(DevProblem d, DevSampl
   double v[3] = {0.0, 0.0, 0.0};
   for (int rl = 0; rl < kSliceRows; ++rl) {
     const int64_t row = slice * kSliceRows + rl;
-    const double ax = mp_row(d, m, off, rl, w, Xs, m.x, row, true, pk, k);
+    const double ax = mp_row<double>(d, m, off, rl, w, Xs, m.x, row, true, pk, k);
     const int64_t idx = row * W + k;
     const double b = m.b[idx];
     const double r = b - ax;
@@ -147,8 +169,11 @@ __global__ void __launch_bounds__(kTileRows) k_mp_cg_init(DevProblem d, DevSampl
   }
 }
 
-// q_k = A_k p_k and alpha per (subdomain, candidate) still iterating.
-__global__ void __launch_bounds__(kTileRows) k_mp_cg_spmv(DevProblem d, DevSample m) {
+// q_k = A_k p_k and the tile partials of p.q per (subdomain, candidate)
+// still iterating (T = double: FP64 batch; float: the inner solve of the
+// mixed batch).
+template <class T>
+__global__ void __launch_bounds__(kTileRows) k_mp_cg_spmv(DevProblem d, DevSample m, MpVec<T> v) {
   __shared__ double sm[1][kTileSlices][W];
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
@@ -160,22 +185,26 @@ __global__ void __launch_bounds__(kTileRows) k_mp_cg_spmv(DevProblem d, DevSampl
   const int64_t off = d.slice_off[slice];
   const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
   const int64_t t0 = d.sub_tile0[s];
-  const double* Xs = m.pd + t0 * kTileRows * W;
+  const T* Xs = v.pd + t0 * kTileRows * W;
   const double pk = m.psamp[k];
-  double v[1] = {0.0};
+  const T sc = sizeof(T) == 4 ? (T)m.sc[sk] : T(1);
+  MpDot<T> pq;
   for (int rl = 0; rl < kSliceRows; ++rl) {
     const int64_t row = slice * kSliceRows + rl;
-    const double q = mp_row(d, m, off, rl, w, Xs, m.pd, row, true, pk, k);
+    const T q = mp_row<T>(d, m, off, rl, w, Xs, v.pd, row, true, pk, k);
     const int64_t idx = row * W + k;
-    m.q[idx] = q;
-    v[0] += m.pd[idx] * q;
+    v.q[idx] = q;
+    pq.add(v.pd[idx], q, sc);
   }
-  lane_block_sum<1>(v, sm);
-  if (warp == 0) m.part0[tile * W + k] = v[0];
+  double acc[1] = {(double)pq.acc * (sizeof(T) == 4 ? m.isc2[sk] : 1.0)};
+  lane_block_sum<1>(acc, sm);
+  if (warp == 0) m.part0[tile * W + k] = acc[0];
 }
 
-// x += alpha p, r -= alpha q, z = D_k^-1 r; rho, ||r||^2, stop test, beta.
-__global__ void __launch_bounds__(kTileRows) k_mp_cg_update(DevProblem d, DevSample m) {
+// x += alpha p, r -= alpha q, z = D_k^-1 r and the tile partials of r.z and
+// ||r||^2 per (subdomain, candidate).
+template <class T>
+__global__ void __launch_bounds__(kTileRows) k_mp_cg_update(DevProblem d, DevSample m, MpVec<T> v) {
   __shared__ double sm[2][kTileSlices][W];
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
@@ -183,35 +212,86 @@ __global__ void __launch_bounds__(kTileRows) k_mp_cg_update(DevProblem d, DevSam
   const int64_t sk = (int64_t)s * W + k;
   const int act = m.active[sk];
   if (__any_sync(0xffffffffu, act)) {
-    const double alpha = m.alpha[sk];
+    const T alpha = (T)m.alpha[sk];
     const double pk = m.psamp[k];
-    double v[2] = {0.0, 0.0};
+    const T sc = sizeof(T) == 4 ? (T)m.sc[sk] : T(1);
+    MpDot<T> rz, rr;
     const int64_t slice = tile * kTileSlices + warp;
     for (int rl = 0; rl < kSliceRows; ++rl) {
       const int64_t row = slice * kSliceRows + rl;
       const int64_t idx = row * W + k;
       if (act) {
-        m.x[idx] = fma(alpha, m.pd[idx], m.x[idx]);
-        const double r = fma(-alpha, m.q[idx], m.r[idx]);
-        const double z = mp_dinv(d, m, row, pk) * r;
-        m.r[idx] = r;
-        m.z[idx] = z;
-        v[0] += r * z;
-        v[1] += r * r;
+        v.x[idx] = fma(alpha, v.pd[idx], v.x[idx]);
+        const T r = fma(-alpha, v.q[idx], v.r[idx]);
+        const T z = (T)mp_dinv(d, m, row, pk) * r;
+        v.r[idx] = r;
+        v.z[idx] = z;
+        rz.add(r, z, sc);
+        rr.add(r, r, sc);
       }
     }
-    lane_block_sum<2>(v, sm);
+    const double un = sizeof(T) == 4 ? m.isc2[sk] : 1.0;
+    double acc[2] = {(double)rz.acc * un, (double)rr.acc * un};
+    lane_block_sum<2>(acc, sm);
     if (warp == 0) {
-      m.part1[tile * W + k] = v[0];
-      m.part2[tile * W + k] = v[1];
+      m.part1[tile * W + k] = acc[0];
+      m.part2[tile * W + k] = acc[1];
     }
   }
+}
+
+// Mixed batch, start of a refinement step: FP64 defect d_k = b_k - A_k x_k,
+// then the FP32 CG on A_k e = d_k from e = 0 (r = d, z = D_k^-1 r, p = z)
+// and the tile partials of ||d||^2, ||b||^2 and r.z.
+__global__ void __launch_bounds__(kTileRows) k_mp_cg_init_mixed(DevProblem d, DevSample m) {
+  __shared__ double sm[3][kTileSlices][W];
+  const int64_t tile = blockIdx.x;
+  const int s = d.tile_sub[tile];
+  const int warp = threadIdx.x >> 5, k = threadIdx.x & 31;
+  const int64_t slice = tile * kTileSlices + warp;
+  const int64_t off = d.slice_off[slice];
+  const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
+  const int64_t t0 = d.sub_tile0[s];
+  const double* Xs = m.x + t0 * kTileRows * W;
+  const double pk = m.psamp[k];
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int rl = 0; rl < kSliceRows; ++rl) {
+    const int64_t row = slice * kSliceRows + rl;
+    const double ax = mp_row<double>(d, m, off, rl, w, Xs, m.x, row, true, pk, k);
+    const int64_t idx = row * W + k;
+    const double b = m.b[idx];
+    const double dfc = b - ax;
+    const float r = (float)dfc;
+    const float z = (float)mp_dinv(d, m, row, pk) * r;
+    m.x32[idx] = 0.f;
+    m.r32[idx] = r;
+    m.z32[idx] = z;
+    m.pd32[idx] = z;
+    acc[0] += dfc * dfc;
+    acc[1] += b * b;
+    acc[2] += (double)r * (double)z;
+  }
+  lane_block_sum<3>(acc, sm);
+  if (warp == 0) {
+    m.part0[tile * W + k] = acc[0];
+    m.part1[tile * W + k] = acc[1];
+    m.part2[tile * W + k] = acc[2];
+  }
+}
+
+// Mixed batch, end of the refinement step: x_k += e_k in FP64.
+__global__ void k_mp_mixed_correct(DevSample m, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) m.x[i] += (double)m.x32[i];
 }
 
 // Per-subdomain finalisers, one warp per subdomain and one lane per
 // candidate: the tile partials are added in a fixed order.
 
-__global__ void k_mp_fin_init(DevProblem d, DevSample m, unsigned long long cond, int use_cond) {
+// mixed (the refinement forms): the partials are ||d||^2, ||b||^2, r.z with
+// d the defect; the inner solve's reference norm is ||d|| and a candidate
+// whose defect meets inner_rtol on this subdomain is not corrected.
+__global__ void k_mp_fin_init(DevProblem d, DevSample m, int mixed, unsigned long long cond, int use_cond) {
   __shared__ bool flag;
   const int warp = threadIdx.x >> 5, k = threadIdx.x & 31;
   const int s = blockIdx.x * kTileSlices + warp;
@@ -222,11 +302,20 @@ __global__ void k_mp_fin_init(DevProblem d, DevSample m, unsigned long long cond
     const double rz = lane_sum_tiles(m.part2, t0, nt, k);
     const int64_t sk = (int64_t)s * W + k;
     m.rr[sk] = rr;
-    m.bb[sk] = bb;
+    m.bb[sk] = mixed ? rr : bb;
     m.rho[sk] = rz;
     m.beta[sk] = 0.0;
     m.iters[sk] = 0;
-    const int act = !m.done[k] && !(rr <= d.ctl->tau2 * bb);
+    // scale of the FP32 dot products: sc = 2^-e with 2^e ~ rms of the defect
+    int e = 0;
+    const double ms = rr / (double)(nt * kTileRows);
+    if (mixed && ms > 0.0 && isfinite(ms)) {
+      frexp(sqrt(ms), &e);
+      e = max(-120, min(120, e));
+    }
+    m.sc[sk] = (float)ldexp(1.0, -e);
+    m.isc2[sk] = ldexp(1.0, 2 * e);
+    const int act = !m.done[k] && (mixed ? (!(rr <= d.ctl->tau2_outer * bb) && rz > 0.0) : !(rr <= d.ctl->tau2 * bb));
     m.active[sk] = act;
     const unsigned bal = __ballot_sync(0xffffffffu, act);
     if (k == 0 && bal) atomicAdd(&d.ctl->n_active, __popc(bal));
@@ -290,17 +379,18 @@ __global__ void k_mp_fin_beta(DevProblem d, DevSample m, unsigned long long cond
 }
 
 // p = z + beta p for the (subdomain, candidate) pairs still iterating.
-__global__ void __launch_bounds__(kTileRows) k_mp_cg_direction(DevProblem d, DevSample m) {
+template <class T>
+__global__ void __launch_bounds__(kTileRows) k_mp_cg_direction(DevProblem d, DevSample m, MpVec<T> v) {
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
   const int warp = threadIdx.x >> 5, k = threadIdx.x & 31;
   const int64_t sk = (int64_t)s * W + k;
   if (!m.active[sk]) return;
-  const double beta = m.beta[sk];
+  const T beta = (T)m.beta[sk];
   const int64_t slice = tile * kTileSlices + warp;
   for (int rl = 0; rl < kSliceRows; ++rl) {
     const int64_t idx = (slice * kSliceRows + rl) * W + k;
-    m.pd[idx] = fma(beta, m.pd[idx], m.z[idx]);
+    v.pd[idx] = fma(beta, v.pd[idx], v.z[idx]);
   }
 }
 
@@ -337,7 +427,7 @@ __global__ void k_mp_average(DevProblem d, DevSample m) {
     if (c0 == c1) continue;
     double s = 0.0;
     for (int32_t c = c0; c < c1; ++c) s += m.x[(int64_t)d.cp_idx[c] * W + k];
-    const double ub = s / (double)(c1 - c0);
+    const double ub = copy_mean(s, c1 - c0);
     for (int32_t c = c0; c < c1; ++c) m.w[(int64_t)d.cp_idx[c] * W + k] = ub;
   }
 }
@@ -354,7 +444,7 @@ __global__ void __launch_bounds__(kTileRows) k_mp_spmv_k(DevProblem d, DevSample
   const double* Xs = m.w + t0 * kTileRows * W;
   for (int rl = 0; rl < kSliceRows; ++rl) {
     const int64_t row = slice * kSliceRows + rl;
-    m.y[row * W + k] = mp_row(d, m, off, rl, w, Xs, m.w, row, false, 0.0, k);
+    m.y[row * W + k] = mp_row<double>(d, m, off, rl, w, Xs, m.w, row, false, 0.0, k);
   }
 }
 
@@ -418,25 +508,37 @@ cudaError_t launch_mp_start(const DevProblem& d, const DevSample& m, cudaStream_
 }
 
 cudaError_t launch_mp_rhs_init(const DevProblem& d, const DevSample& m, cudaStream_t s, unsigned long long cond,
-                               int use_cond) {
+                               int use_cond, int fp32, int refine) {
   k_mp_rhs_gather<<<blocks_for((d.n_irow > 0 ? d.n_irow : 1) * (int64_t)32, 256), 256, 0, s>>>(d, m);
-  k_mp_cg_init<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m);
-  k_mp_fin_init<<<fin_blocks(d), kTileRows, 0, s>>>(d, m, cond, use_cond);
+  if (fp32) k_mp_cg_init_mixed<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m);
+  else k_mp_cg_init<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m);
+  k_mp_fin_init<<<fin_blocks(d), kTileRows, 0, s>>>(d, m, refine, cond, use_cond);
   return cudaGetLastError();
 }
 
-cudaError_t launch_mp_cg_iteration(const DevProblem& d, const DevSample& m, cudaStream_t s,
-                                   unsigned long long cond, int use_cond) {
-  k_mp_cg_spmv<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m);
+template <class T>
+static void mp_cg_iteration(const DevProblem& d, const DevSample& m, MpVec<T> v, cudaStream_t s,
+                            unsigned long long cond, int use_cond) {
+  k_mp_cg_spmv<T><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m, v);
   k_mp_fin_alpha<<<fin_blocks(d), kTileRows, 0, s>>>(d, m);
-  k_mp_cg_update<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m);
+  k_mp_cg_update<T><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m, v);
   k_mp_fin_beta<<<fin_blocks(d), kTileRows, 0, s>>>(d, m, cond, use_cond);
-  k_mp_cg_direction<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m);
+  k_mp_cg_direction<T><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m, v);
+}
+
+cudaError_t launch_mp_cg_iteration(const DevProblem& d, const DevSample& m, cudaStream_t s,
+                                   unsigned long long cond, int use_cond, int mixed) {
+  if (mixed) mp_cg_iteration<float>(d, m, MpVec<float>{m.x32, m.r32, m.z32, m.pd32, m.q32}, s, cond, use_cond);
+  else mp_cg_iteration<double>(d, m, MpVec<double>{m.x, m.r, m.z, m.pd, m.q}, s, cond, use_cond);
   return cudaGetLastError();
 }
 
 cudaError_t launch_mp_exchange_residual(const DevProblem& d, const DevSample& m, cudaStream_t s,
-                                        unsigned long long cond, int use_cond) {
+                                        unsigned long long cond, int use_cond, int mixed) {
+  if (mixed) {
+    const int64_t n = d.n_tiles * (int64_t)kTileRows * W;
+    k_mp_mixed_correct<<<blocks_for(n, 256), 256, 0, s>>>(m, n);
+  }
   if (d.n_fent) k_mp_exchange<<<blocks_for(d.n_fent * (int64_t)32, 256), 256, 0, s>>>(d, m);
   k_mp_average<<<kNodeBlocks, 256, 0, s>>>(d, m);
   k_mp_spmv_k<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, m);

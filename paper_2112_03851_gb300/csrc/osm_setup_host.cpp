@@ -245,8 +245,9 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
   struct IfaceRow {
     int32_t row;
     double mdiag;
+    double tdiag[4];                  // diagonal of M_lo, M_hi, S_lo, S_hi
     std::vector<int32_t> col;
-    std::vector<double> m, kv;
+    std::vector<double> m, kv, tc;    // tc: 4 per entry (M_lo, M_hi, S_lo, S_hi)
     std::vector<int64_t> pos, pos32;
   };
   std::vector<std::vector<IfaceRow>> irows(nsub);
@@ -270,7 +271,11 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
                          S.iface[4] && k == S.k0, S.iface[5] && k == S.k1};
       bool is_if = on_face[0] || on_face[1] || on_face[2] || on_face[3] || on_face[4] || on_face[5];
       IfaceRow ir;
-      if (is_if) { ir.row = (int32_t)(S.voff + r); ir.mdiag = 0.0; }
+      if (is_if) {
+        ir.row = (int32_t)(S.voff + r);
+        ir.mdiag = 0.0;
+        for (double& t : ir.tdiag) t = 0.0;
+      }
       int jn = 0;
       for (int kk = std::max(S.k0, k - reach(k)); kk <= std::min(S.k1, k + reach(k)); ++kk)
         for (int jj = std::max(S.j0, j - reach(j)); jj <= std::min(S.j1, j + reach(j)); ++jj)
@@ -289,23 +294,45 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
             if (want_fp32) hp.vals32[cpos] = (float)v;
             if (col == r) hp.kdiag[S.voff + r] = v;
             if (is_if) {
-              double mv = 0.0;
-              if ((on_face[0] && ii == S.i0) || (on_face[1] && ii == S.i1))
-                mv += w.by.m(bj, bb) * w.bz.m(ck, cc);
-              if ((on_face[2] && jj == S.j0) || (on_face[3] && jj == S.j1))
-                mv += w.bx.m(ai, aa) * w.bz.m(ck, cc);
-              if ((on_face[4] && kk == S.k0) || (on_face[5] && kk == S.k1))
-                mv += w.bx.m(ai, aa) * w.by.m(bj, bb);
-              bool coupled = ((on_face[0] && ii == S.i0) || (on_face[1] && ii == S.i1) ||
-                              (on_face[2] && jj == S.j0) || (on_face[3] && jj == S.j1) ||
-                              (on_face[4] && kk == S.k0) || (on_face[5] && kk == S.k1));
+              // face mass (Ma (x) Mb) and tangential stiffness (Ka (x) Mb + Ma (x) Kb)
+              // of every face of this subdomain holding both nodes; faces 1, 3, 5
+              // (+x, +y, +z) have this subdomain on their lower side.
+              double mv = 0.0, t4[4] = {0.0, 0.0, 0.0, 0.0};
+              bool coupled = false;
+              for (int fc = 0; fc < 6; ++fc) {
+                if (!on_face[fc]) continue;
+                const int ax = fc >> 1;
+                const int plane = ax == 0 ? (fc & 1 ? S.i1 : S.i0) : ax == 1 ? (fc & 1 ? S.j1 : S.j0) : (fc & 1 ? S.k1 : S.k0);
+                const int other = ax == 0 ? ii : ax == 1 ? jj : kk;
+                if (other != plane) continue;
+                coupled = true;
+                double fm, fs;
+                if (ax == 0) {
+                  fm = w.by.m(bj, bb) * w.bz.m(ck, cc);
+                  fs = w.by.k(bj, bb) * w.bz.m(ck, cc) + w.by.m(bj, bb) * w.bz.k(ck, cc);
+                } else if (ax == 1) {
+                  fm = w.bx.m(ai, aa) * w.bz.m(ck, cc);
+                  fs = w.bx.k(ai, aa) * w.bz.m(ck, cc) + w.bx.m(ai, aa) * w.bz.k(ck, cc);
+                } else {
+                  fm = w.bx.m(ai, aa) * w.by.m(bj, bb);
+                  fs = w.bx.k(ai, aa) * w.by.m(bj, bb) + w.bx.m(ai, aa) * w.by.k(bj, bb);
+                }
+                mv += fm;
+                const int side = (fc & 1) ? 0 : 1;   // 0: lower side, 1: upper side
+                t4[side] += fm;
+                t4[2 + side] += fs;
+              }
               if (coupled) {
                 ir.col.push_back((int32_t)(S.voff + col));
                 ir.m.push_back(mv);
                 ir.kv.push_back(v);
+                ir.tc.insert(ir.tc.end(), t4, t4 + 4);
                 ir.pos.push_back(vpos);
                 ir.pos32.push_back(cpos);
-                if (col == r) ir.mdiag = mv;
+                if (col == r) {
+                  ir.mdiag = mv;
+                  for (int t = 0; t < 4; ++t) ir.tdiag[t] = t4[t];
+                }
               }
             }
             ++jn;
@@ -346,7 +373,7 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
   // ---- faces (canonical face layout) with their tangential 1-D masses
   hp.face_s.clear(); hp.face_t.clear(); hp.face_n.clear(); hp.face_eo.clear();
   hp.fent_face.clear(); hp.fent_row_s.clear(); hp.fent_row_t.clear();
-  hp.fm_ptr.assign(1, 0); hp.fm_col.clear(); hp.fm_val.clear();
+  hp.fm_ptr.assign(1, 0); hp.fm_col.clear(); hp.fm_val.clear(); hp.fs_val.clear();
   std::vector<std::pair<int32_t, int32_t>> lam_rows;  // (vector row, lam index)
   auto add_face = [&](int s, int t, int axis, int plane, int a0, int a1, int b0, int b1) {
     const SubInfo& S = hp.sub[s];
@@ -397,6 +424,8 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
             if (m2 < 0) continue;
             hp.fm_col.push_back((int32_t)(eo + m2));
             hp.fm_val.push_back(ba.m(a - oa, aa2 - oa) * bb.m(b - ob, bb2 - ob));
+            hp.fs_val.push_back(ba.k(a - oa, aa2 - oa) * bb.m(b - ob, bb2 - ob) +
+                                ba.m(a - oa, aa2 - oa) * bb.k(b - ob, bb2 - ob));
           }
         hp.fm_ptr.push_back((int32_t)hp.fm_col.size());
       }
@@ -428,8 +457,9 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
   if ((int64_t)hp.fm_col.size() >= ((int64_t)1 << 31)) return "too many face mass entries";
 
   // ---- interface rows: Robin entries and received lam indices
-  hp.irow.clear(); hp.irow_sub.clear(); hp.irow_mdiag.clear();
+  hp.irow.clear(); hp.irow_sub.clear(); hp.irow_mdiag.clear(); hp.irow_tdiag.clear();
   hp.im_ptr.assign(1, 0); hp.im_col.clear(); hp.im_val.clear(); hp.im_pos.clear(); hp.im_kval.clear();
+  hp.im_tc.clear();
   hp.im_pos32.clear();
   std::stable_sort(lam_rows.begin(), lam_rows.end(),
                    [](const std::pair<int32_t, int32_t>& x, const std::pair<int32_t, int32_t>& y) {
@@ -444,6 +474,8 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
       hp.irow.push_back(ir.row);
       hp.irow_sub.push_back(s);
       hp.irow_mdiag.push_back(ir.mdiag);
+      hp.irow_tdiag.insert(hp.irow_tdiag.end(), ir.tdiag, ir.tdiag + 4);
+      hp.im_tc.insert(hp.im_tc.end(), ir.tc.begin(), ir.tc.end());
       for (size_t e = 0; e < ir.col.size(); ++e) {
         hp.im_col.push_back(ir.col[e]);
         hp.im_val.push_back(ir.m[e]);
@@ -466,9 +498,9 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
 }
 
 // Residual blocks of nodes [n0, n1) of instance `inst`: about one block per
-// 2048 nodes, at least one.
+// 256 nodes (one per thread of a 256-thread block), at least one.
 static void add_rblocks(HostProblem& hp, int inst, int64_t n0, int64_t n1) {
-  const int64_t per = 2048;
+  const int64_t per = 256;
   const int64_t nb = std::max<int64_t>(1, (n1 - n0 + per - 1) / per);
   for (int64_t b = 0; b < nb; ++b) {
     hp.rblock_inst.push_back(inst);
@@ -542,6 +574,8 @@ std::string merge_problems(std::vector<HostProblem>& parts, HostProblem& out) {
     append_shift(o.irow, p.irow, (int32_t)vec_off);
     append_shift(o.irow_sub, p.irow_sub, sub_off);
     append(o.irow_mdiag, p.irow_mdiag);
+    append(o.irow_tdiag, p.irow_tdiag);
+    append(o.im_tc, p.im_tc);
     for (size_t k = 1; k < p.ilam_ptr.size(); ++k) o.ilam_ptr.push_back((int32_t)(p.ilam_ptr[k] + ilam_off));
     append_shift(o.ilam, p.ilam, (int32_t)(2 * fent_off));
     for (size_t k = 1; k < p.im_ptr.size(); ++k) o.im_ptr.push_back((int32_t)(p.im_ptr[k] + im_off));
@@ -560,6 +594,7 @@ std::string merge_problems(std::vector<HostProblem>& parts, HostProblem& out) {
     for (size_t k = 1; k < p.fm_ptr.size(); ++k) o.fm_ptr.push_back((int32_t)(p.fm_ptr[k] + fm_off));
     append_shift(o.fm_col, p.fm_col, (int32_t)fent_off);
     append(o.fm_val, p.fm_val);
+    append(o.fs_val, p.fs_val);
     for (size_t k = 1; k < p.cp_ptr.size(); ++k) o.cp_ptr.push_back((int32_t)(p.cp_ptr[k] + cp_off));
     append_shift(o.cp_idx, p.cp_idx, (int32_t)vec_off);
     for (int s = 0; s < p.nsub; ++s) o.sub_inst.push_back(i);

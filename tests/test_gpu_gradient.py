@@ -153,3 +153,36 @@ def test_gradient_against_finite_differences_full_size(osm):
         Js.append(0.5 * float(((sol.gravity(ph) - g_obs) ** 2).sum()))
     fd = (Js[0] - Js[1]) / 2e-6
     assert abs(fd - grad @ d) <= 0.1 * gnorm
+
+
+def test_truncated_schwarz_p_gradient(osm):
+    """dJ_N/dp of the misfit after exactly N Schwarz iterations, by reverse-
+    mode Schwarz on the GPU, against central differences of the oracle's own
+    truncated sequential Schwarz (subdomain solves to 1e-14 on both sides)."""
+    prob = gen.regional_problem(nx=12, ny=10, nz=8, sx=3, sy=2, sz=2, p=2.0, seed=4, lx=10.0, ly=8.0, lz=3.0)
+    st = gen.surface_stations(8, lx=10.0, ly=8.0, z=3.0)
+    M = oracle.Misfit(prob.xc, prob.yc, prob.zc, st)
+    g_obs = M.gravity(prob.drho * 1.1)
+    N, p0 = 10, 2.0
+
+    def J_oracle(p):
+        S = oracle.Schwarz.from_problem(prob, p=p)
+        for _ in range(N):
+            S.iterate(inner_rtol=1e-14)
+        phi, _ = S.residual()
+        r = M.B @ phi[M.G.gnode] - g_obs
+        return 0.5 * float(r @ r)
+
+    sol = osm.Solver.from_problem(prob, p=p0, inner_rtol=1e-14, max_outer=400)   # the solve below needs 175
+    sol.set_stations(st)
+    J, dJdp = sol.grad_p(_t(g_obs), N)
+    J_ref = J_oracle(p0)
+    assert abs(J - J_ref) <= 1e-9 * J_ref
+    h = 1e-5 * p0
+    fd = (J_oracle(p0 + h) - J_oracle(p0 - h)) / (2 * h)
+    assert abs(fd) > 1e-6 * J_ref / p0          # a genuinely p-dependent truncated misfit
+    assert abs(dJdp - fd) <= 1e-5 * abs(fd), (dJdp, fd)
+    # the handle is back in its zero state and solves like a fresh one
+    _, n, rel = sol.solve(1e-10)
+    _, n_ref, _, _ = oracle.Schwarz.from_problem(prob, p=p0).solve(inner_rtol=1e-14, rtol=1e-10, max_outer=400)
+    assert rel <= 1e-10 and abs(n - n_ref) <= 1, (n, n_ref)

@@ -120,3 +120,32 @@ def test_mixed_layered64_full_size_residual(osm):
     assert rel <= 1e-8
     G = oracle.GlobalSystem(prob.xc, prob.yc, prob.zc, prob.drho)
     assert G.residual(phi.cpu().numpy()) <= 1.001e-8
+
+
+@pytest.mark.parametrize("case", ["sphere16", "uneven"])
+def test_16bit_columns_give_identical_results(osm, case):
+    """The SpMVs with 16-bit column indices read the same entries in the same
+    order as with 32-bit ones: the FP32 and FP64 operators and a whole mixed
+    solve are bit-identical."""
+    import torch
+    prob = gen.sphere_problem(16, 2, 10.0) if case == "sphere16" else small_uneven()
+    a = osm.Solver.from_problem(prob, p=3.3, prec="mixed", index16=1, autotune=0, inner_rtol=1e-12)
+    b = osm.Solver.from_problem(prob, p=3.3, prec="mixed", index16=0, autotune=0, inner_rtol=1e-12)
+    assert a.info["col_bytes_fp64"] == 2 and a.info["col_bytes_fp32"] == 2
+    assert b.info["col_bytes_fp64"] == 4 and b.info["col_bytes_fp32"] == 4
+    x = torch.from_numpy(np.random.default_rng(5).standard_normal(a.info["n_local"])).cuda()
+    for op in (0, 1, 2):
+        assert bool((a.apply(x, op=op) == b.apply(x, op=op)).all()), op
+    pa, na, ra = a.solve(rtol=1e-10)
+    pb, nb, rb = b.solve(rtol=1e-10)
+    assert na == nb and ra == rb and bool((pa == pb).all())
+
+
+def test_32bit_columns_for_large_subdomains(osm):
+    """A subdomain of more than 65,536 padded rows keeps 32-bit indices."""
+    prob = gen.sphere_problem(26, 1, 10.0)            # one subdomain, 51^3 = 132,651 unknowns
+    sol = osm.Solver.from_problem(prob, prec="mixed", index16=1, inner_rtol=1e-12)
+    assert sol.info["col_bytes_fp64"] == 4 and sol.info["col_bytes_fp32"] == 4
+    phi, n, rel = sol.solve(rtol=1e-9)
+    G = oracle.GlobalSystem(prob.xc, prob.yc, prob.zc, prob.drho)
+    assert G.residual(phi.cpu().numpy()) <= 1.001e-9

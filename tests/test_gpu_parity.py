@@ -211,3 +211,22 @@ def test_layered64_full_size_residual(osm):
     assert rel <= 1e-8
     G = oracle.GlobalSystem(prob.xc, prob.yc, prob.zc, prob.drho)
     assert G.residual(phi.cpu().numpy()) <= 1.001e-8
+
+
+def test_spmv_variants_agree(osm):
+    """The autotuner's SpMV variants (one or two SELL slices per warp) give
+    bit-identical operator results (same per-row summation order) and the
+    same solve up to reduction rounding."""
+    import torch
+    prob = small_uneven()
+    sols = [osm.Solver.from_problem(prob, p=2.0, autotune=a, prec="mixed", inner_rtol=1e-13) for a in (0, 2, 1)]
+    assert sols[0].info["spmv_variant_fp64"] == 1 and sols[1].info["spmv_variant_fp64"] == 2
+    assert sols[2].info["spmv_variant_fp64"] in (1, 2) and min(sols[2].info["spmv_ms_fp64"]) > 0
+    rng = np.random.default_rng(1)
+    x = torch.from_numpy(rng.standard_normal(sols[0].info["n_local"])).cuda()
+    for op in (0, 1, 2):
+        ys = [sol.apply(x, op=op) for sol in sols]
+        assert torch.equal(ys[0], ys[1]) and torch.equal(ys[0], ys[2])
+    phis = [sol.solve(rtol=1e-11)[0] for sol in sols]
+    for ph in phis[1:]:
+        assert float((ph - phis[0]).norm() / phis[0].norm()) <= 1e-9

@@ -85,3 +85,37 @@ def test_sample_rejects_bad_p(osm):
     for bad in ([1.0, -2.0], [float("nan")], []):
         with pytest.raises(osm.OsmError):
             sol.sample_p(np.array(bad, dtype=np.float64))
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64_refine"])
+def test_sample_in_refinement_modes_matches_single_solves(osm, prec):
+    """On a mixed (FP32 inner) or FP64-refinement handle every candidate runs
+    that handle's algorithm: same Schwarz iteration count as a single solve
+    (+-1 for rounding of the reductions) and a residual at rtol."""
+    prob = small_uneven()
+    ps = gen.log_uniform_p(3, 5, 0.5, 20.0)
+    sol = osm.Solver.from_problem(prob, prec=prec, mixed_inner_rtol=0.3, inner_rtol=1e-12, max_outer=1500)
+    iters, rel, best = sol.sample_p(ps, rtol=1e-9, max_outer=1500)
+    for k, p in enumerate(ps):
+        sol.set_robin(float(p))
+        _, n1, r1 = sol.solve(rtol=1e-9, allow_noconv=True)
+        assert abs(int(iters[k]) - n1) <= max(1, n1 // 50), (k, p, iters[k], n1)
+        if rel[k] <= 1e-9:
+            assert r1 <= 1e-9
+    assert best >= 0 and rel[best] <= 1e-9
+
+
+def test_cma_es_search_with_batched_evaluation(osm):
+    """CMA-ES (Sec. 4) over log p with the measured Schwarz iteration count as
+    the cost, each generation one batched run: it must reach a p at least as
+    good as the best of a log-uniform sample of the same budget's first
+    generation."""
+    from paper_2112_03851_gb300 import search
+    prob = gen.sphere_problem(8, 2, 4.0)
+    sol = osm.Solver.from_problem(prob, inner_rtol=1e-10, max_outer=400)
+    p_best, res = search.search_p(sol, p0=1.0, sigma0=1.5, popsize=16, generations=4, rtol=1e-8, max_outer=400)
+    iters, rel, _ = sol.sample_p(np.array([p_best]), rtol=1e-8, max_outer=400)
+    ps = gen.log_uniform_p(11, 16, 0.1, 100.0)
+    it_s, rel_s, best_s = sol.sample_p(ps, rtol=1e-8, max_outer=400)
+    assert rel[0] <= 1e-8 and iters[0] <= it_s[best_s]
+    assert res.evaluations == 16 * res.iterations

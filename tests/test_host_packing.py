@@ -88,6 +88,24 @@ def test_face_masses_match_oracle(osm, name):
         assert np.abs((M - M_ref).toarray()).max() <= 1e-15 * np.abs(M_ref).max(), f
 
 
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_second_order_local_systems_and_face_stiffness_match_oracle(osm, name):
+    """Split transmission entries (lower/upper side, face mass and tangential
+    stiffness) reassembled with unsymmetric oo2 coefficients equal the
+    oracle's local matrices; every face stiffness equals the oracle's."""
+    prob = _with_cuts(CASES[name](), name)
+    tc = (1.3, 0.21, 0.4, 0.77)
+    S = oracle.Schwarz(prob.xc, prob.yc, prob.zc, prob.drho, prob.cx, prob.cy, prob.cz, tc=tc)
+    for s in range(S.nsub):
+        A_ref, _, _, _ = S.sub_export(s)
+        A, _ = osm.host_local_system(prob.xc, prob.yc, prob.zc, prob.drho, prob.cx, prob.cy, prob.cz, 0.0, s, tc=tc)
+        assert np.abs((A - A_ref).toarray()).max() <= 1e-13 * np.abs(A_ref).max(), s
+    for f in range(S.nface):
+        S_ref = S.face_stiffness_export(f)
+        _, Sf = osm.host_face_stiffness(prob.xc, prob.yc, prob.zc, prob.drho, prob.cx, prob.cy, prob.cz, f)
+        assert np.abs((Sf - S_ref).toarray()).max() <= 1e-14 * np.abs(S_ref).max(), f
+
+
 def test_bad_inputs_are_rejected(osm):
     prob = gen.sphere_problem(4, 2, 1.0)
     with pytest.raises(osm.OsmError):

@@ -1,0 +1,67 @@
+"""The stochastic search of Sec. 4 (CMA-ES) and its Fourier cost, pinned to
+the paper's Table 1 (tests/golden/table1_optimized_coefficients.json).
+
+The frequency band is not printed; [0.0174, 1.915] is the band for which the
+symmetric zeroth-order row is exact (its optimum is p = sqrt(kmin kmax) with
+rho = ((sqrt(kmax) - sqrt(kmin)) / (sqrt(kmax) + sqrt(kmin)))^2), and the
+second-order operator enters as the symbol p + q k^2.
+"""
+import json
+import math
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from paper_2112_03851_gb300 import search
+
+TABLE = json.loads((Path(__file__).parent / "golden" / "table1_optimized_coefficients.json").read_text())["rows"]
+KMIN, KMAX = 0.0174, 1.915
+
+
+def _params(kind, row):
+    return {"oo0_sym": [row["p1"]], "oo0_unsym": [row["p1"], row["p2"]], "oo2_sym": [row["p1"], row["q1"]],
+            "oo2_unsym": [row["p1"], row["q1"], row["p2"], row["q2"]]}[kind]
+
+
+def test_fourier_rate_basics():
+    k = np.geomspace(0.01, 10, 50)
+    # the optimal symbol Lambda = |k| annihilates every mode (Sec. 3)
+    assert np.all(search.fourier_rate(k, k) == 0.0)
+    # zeroth order: ((p - k) / (p + k))^2, below 1 for p > 0
+    r = search.fourier_rate(k, 0.7)
+    assert np.allclose(r, ((0.7 - k) / (0.7 + k)) ** 2) and np.all(r < 1)
+
+
+@pytest.mark.parametrize("kind", sorted(TABLE))
+def test_cost_at_table1_coefficients(kind):
+    row = TABLE[kind]
+    rho = search.fourier_cost(np.log(_params(kind, row)), KMIN, KMAX, kind=kind)
+    assert abs(rho - row["rho_max"]) <= 0.08 * row["rho_max"], (kind, rho)
+
+
+def test_closed_form_of_symmetric_oo0():
+    p = math.sqrt(KMIN * KMAX)
+    rho = ((math.sqrt(KMAX) - math.sqrt(KMIN)) / (math.sqrt(KMAX) + math.sqrt(KMIN))) ** 2
+    assert abs(p - TABLE["oo0_sym"]["p1"]) < 2e-4 and abs(rho - TABLE["oo0_sym"]["rho_max"]) < 2e-4
+    assert abs(search.fourier_cost([math.log(p)], KMIN, KMAX, nk=20000) - rho) < 1e-6
+
+
+def test_cma_es_finds_the_symmetric_oo0_optimum():
+    x, f, res = search.optimise_fourier("oo0_sym", KMIN, KMAX, seed=1)
+    assert abs(x[0] - TABLE["oo0_sym"]["p1"]) < 1e-3 and abs(f - TABLE["oo0_sym"]["rho_max"]) < 1e-3
+    assert res.stop in ("tol", "sigma")
+
+
+@pytest.mark.parametrize("kind", ["oo0_unsym", "oo2_sym"])
+def test_cma_es_matches_or_beats_table1(kind):
+    """Under this reading of the band the search reaches a maximal rate no
+    worse than the one Table 1's coefficients give."""
+    x, f, res = search.optimise_fourier(kind, KMIN, KMAX, seed=0, max_iter=400)
+    ref = search.fourier_cost(np.log(_params(kind, TABLE[kind])), KMIN, KMAX, kind=kind)
+    assert f <= ref + 1e-9
+
+
+def test_cma_es_on_a_quadratic():
+    res = search.cma_es(lambda X: np.sum((X - 3.0) ** 2, axis=1), np.zeros(3), 1.0, popsize=12, seed=2)
+    assert np.allclose(res.x, 3.0, atol=1e-5) and res.stop in ("tol", "sigma")
