@@ -219,6 +219,20 @@ osm_status osm_sample_p(osm_handle h, int32_t n_p, const double *p_host, double 
                         int32_t max_outer, int32_t *iters_host, double *relres_host,
                         int32_t *best_idx);
 
+/*
+ * osm_sample_p with flags.  OSM_SAMPLE_RACE: the search wants the fastest-
+ * converging p (fewest Schwarz iterations, Sec. 4), so a batch stops at the
+ * iteration where its first candidate reaches rtol -- no candidate still
+ * running can need fewer -- and a later batch of 32 stops at the best count
+ * found so far.  The winner and every candidate converging at the same
+ * iteration get exactly their osm_sample_p results; the others report the
+ * iteration and the residual at which they were stopped (relres > rtol).
+ * Unknown flags: OSM_E_ARG.
+ */
+#define OSM_SAMPLE_RACE 1
+osm_status osm_sample_p_ex(osm_handle h, int32_t n_p, const double *p_host, double rtol, int32_t max_outer,
+                           int32_t flags, int32_t *iters_host, double *relres_host, int32_t *best_idx);
+
 /* ----------------------------------------------------------------------
  * Adjoint gradient of a surface-gravity misfit.  The paper's forward model
  * (Sec. 2, solved as in Sec. 3) is differentiated; the paper itself has no

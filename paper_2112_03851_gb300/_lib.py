@@ -23,7 +23,7 @@ EXPORTED = (
     "osm_gravity", "osm_potential_vjp", "osm_grad", "osm_grad_p", "osm_host_local_system", "osm_host_face_system",
     "osm_profile_spmv", "osm_status_string", "osm_last_error", "osm_destroy", "osm_setup_batch",
     "osm_batch_info", "osm_set_robin_inst", "osm_solve_batch", "osm_set_transmission",
-    "osm_host_local_system_tc", "osm_host_face_stiffness",
+    "osm_host_local_system_tc", "osm_host_face_stiffness", "osm_sample_p_ex",
 )
 
 
@@ -98,6 +98,7 @@ def load():
         "osm_set_transmission": (C.c_int, [vp, d, d, d, d]),
         "osm_solve": (C.c_int, [vp, d, vp, vp, vp]),
         "osm_sample_p": (C.c_int, [vp, i32, vp, d, i32, vp, vp, vp]),
+        "osm_sample_p_ex": (C.c_int, [vp, i32, vp, d, i32, i32, vp, vp, vp]),
         "osm_log_uniform_p": (C.c_int, [C.c_uint64, i32, d, d, vp]),
         "osm_apply": (C.c_int, [vp, i32, vp, vp]),
         "osm_apply_noalloc": (C.c_int, [vp, i32, vp, vp]),
@@ -384,15 +385,18 @@ class Solver:
         extra = 12 * i["n_local"] if prec == 2 else 0
         return i["nnz"] * (vb + cb) + i["n_slices"] * 8 + i["n_local"] * 2 * vb + extra
 
-    def sample_p(self, p_values, rtol=1e-8, max_outer=None):
+    def sample_p(self, p_values, rtol=1e-8, max_outer=None, race=False):
+        """Batched evaluation of Robin parameters: (iterations, relres, best
+        index).  race=True stops each batch when its first candidate converges
+        (osm_sample_p_ex with OSM_SAMPLE_RACE)."""
         p = np.ascontiguousarray(p_values, dtype=np.float64)
         n = len(p)
         iters = np.zeros(n, dtype=np.int32)
         rel = np.zeros(n)
         best = C.c_int32(-1)
         mo = self.opts.max_outer if max_outer is None else int(max_outer)
-        self._check(load().osm_sample_p(self._h, n, _ptr(p), float(rtol), mo, _ptr(iters), _ptr(rel),
-                                        C.byref(best)), (OSM_E_NOCONV,))
+        self._check(load().osm_sample_p_ex(self._h, n, _ptr(p), float(rtol), mo, 1 if race else 0, _ptr(iters),
+                                           _ptr(rel), C.byref(best)), (OSM_E_NOCONV,))
         return iters, rel, best.value
 
 

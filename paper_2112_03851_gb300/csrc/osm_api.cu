@@ -114,16 +114,16 @@ osm_status upload_problem(osm_ctx* h) {
   OSM_CUDA(h, upload(h, &sub_tile0, st0));
   d.slice_off = slice_off; d.cols = cols; d.tile_sub = tile_sub; d.sub_tile0 = sub_tile0;
   // blocks of the FP32 CG update: runs of up to kUpdGroup tiles within a subdomain
-  {
+  for (int g : {kUpdGroup, kUpdGroup64}) {
     std::vector<int64_t> ub;
     for (size_t si = 0; si < ns; ++si) {
       const int64_t a0 = st0[si], a1 = st0[si + 1];
-      for (int64_t t = a0; t < a1; t += kUpdGroup) ub.push_back(t);
+      for (int64_t t = a0; t < a1; t += g) ub.push_back(t);
     }
     int64_t* dub;
     OSM_CUDA(h, upload(h, &dub, ub));
-    d.ub_tile0 = dub;
-    d.n_ublocks = (int64_t)ub.size();
+    (g == kUpdGroup ? d.ub_tile0 : d.ub64_tile0) = dub;
+    (g == kUpdGroup ? d.n_ublocks : d.n_ublocks64) = (int64_t)ub.size();
   }
   // 16-bit column indices for the single-path SpMVs when every subdomain fits
   // (the batched p evaluation keeps reading the 32-bit ones)
@@ -221,6 +221,7 @@ osm_status upload_problem(osm_ctx* h) {
   OSM_CUDA(h, dalloc(h, &d.inst_relres, hp.n_inst));
   OSM_CUDA(h, dalloc(h, &d.rpart, d.n_rblocks));
   OSM_CUDA(h, dalloc(h, &d.rpart2, d.n_rblocks));
+  OSM_CUDA(h, dalloc(h, &d.fg, hp.n_nodes));
   OSM_CUDA(h, dalloc(h, &d.hist, h->opts.max_outer > 0 ? h->opts.max_outer : 1));
   OSM_CUDA(h, dalloc(h, &d.ctl, 1));
   OSM_CUDA(h, cudaMallocHost((void**)&h->ctl_host, sizeof(DevCtl)));
@@ -590,6 +591,7 @@ osm_status run_iterations(osm_ctx* h, double rtol, int max_outer) {
   OSM_CUDA(h, cudaMemsetAsync(h->d.inst_iters, 0, sizeof(int32_t) * h->hp.n_inst, h->stream));
   OSM_CUDA(h, cudaMemsetAsync(h->d.inst_relres, 0, sizeof(double) * h->hp.n_inst, h->stream));
   OSM_CUDA(h, cudaMemcpyAsync(h->d.ctl, h->ctl_host, sizeof(DevCtl), cudaMemcpyHostToDevice, h->stream));
+  OSM_CUDA(h, launch_load_nodes(h->d, h->stream));
   if (h->opts.use_graph) {
     osm_status st = build_graph(h);
     if (st != OSM_OK) return st;
@@ -620,8 +622,8 @@ osm_status run_iterations(osm_ctx* h, double rtol, int max_outer) {
 }
 
 // One batch of at most kSampleWidth candidates; the SELL values must hold K.
-osm_status run_sample_batch(osm_ctx* h, int nb, const double* p, double rtol, int max_outer, int32_t* iters,
-                            double* relres) {
+osm_status run_sample_batch(osm_ctx* h, int nb, const double* p, double rtol, int max_outer, int race,
+                            int32_t* iters, double* relres) {
   const int W = kSampleWidth;
   DevSample& m = h->mp;
   std::vector<double> ps(W, 1.0), rel(W, INFINITY);
@@ -635,6 +637,7 @@ osm_status run_sample_batch(osm_ctx* h, int nb, const double* p, double rtol, in
   if (h->hp.n_fent) OSM_CUDA(h, cudaMemsetAsync(m.lam, 0, sizeof(double) * 2 * h->hp.n_fent * W, h->stream));
   OSM_CUDA(h, launch_mp_start(h->d, m, h->stream));
   ctl_reset(h, rtol, max_outer);  // the candidates run the handle's precision mode
+  h->ctl_host->race = race;
   const int mixed = h->opts.prec == OSM_MIXED, refine = h->opts.prec != OSM_FP64;
   OSM_CUDA(h, cudaMemcpyAsync(h->d.ctl, h->ctl_host, sizeof(DevCtl), cudaMemcpyHostToDevice, h->stream));
   if (h->opts.use_graph) {
@@ -1048,7 +1051,14 @@ osm_status osm_inner_iters(osm_handle h, int32_t* iters) {
 
 osm_status osm_sample_p(osm_handle h, int32_t n_p, const double* p_host, double rtol, int32_t max_outer,
                         int32_t* iters_host, double* relres_host, int32_t* best_idx) {
+  return osm_sample_p_ex(h, n_p, p_host, rtol, max_outer, 0, iters_host, relres_host, best_idx);
+}
+
+osm_status osm_sample_p_ex(osm_handle h, int32_t n_p, const double* p_host, double rtol, int32_t max_outer,
+                           int32_t flags, int32_t* iters_host, double* relres_host, int32_t* best_idx) {
   if (!h) return OSM_E_ARG;
+  if (flags & ~OSM_SAMPLE_RACE) return fail(h, OSM_E_ARG, "osm_sample_p_ex: unknown flags");
+  const int race = (flags & OSM_SAMPLE_RACE) != 0;
   if (h->hp.n_inst > 1) return fail(h, OSM_E_STATE, "osm_sample_p needs a single-problem handle");
   if (n_p < 1 || !p_host || !iters_host || !relres_host || !best_idx || !(rtol > 0.0) || max_outer < 1)
     return fail(h, OSM_E_ARG, "osm_sample_p: bad arguments");
@@ -1062,11 +1072,28 @@ osm_status osm_sample_p(osm_handle h, int32_t n_p, const double* p_host, double 
   OSM_CUDA(h, cudaMemsetAsync(h->d.psub, 0, sizeof(double) * h->hp.nsub, h->stream));
   OSM_CUDA(h, cudaMemsetAsync(h->d.tc, 0, sizeof(double) * 4 * h->hp.nsub, h->stream));
   OSM_CUDA(h, launch_set_robin(h->d, h->stream));
+  // candidates run in order of p (a candidate's run does not depend on its
+  // batch companions): lanes of similar p finish their CG at similar steps,
+  // so the lanes still running share cache sectors of the candidate rows
+  std::vector<int32_t> order(n_p);
+  for (int32_t k = 0; k < n_p; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return p_host[a] < p_host[b]; });
+  std::vector<double> ps(n_p), rel_s(n_p);
+  std::vector<int32_t> it_s(n_p);
+  for (int32_t k = 0; k < n_p; ++k) ps[k] = p_host[order[k]];
   int status_or = 0;
+  int cap = max_outer;   // race: later batches cannot beat the best count so far
   for (int32_t b0 = 0; b0 < n_p && st == OSM_OK; b0 += kSampleWidth) {
     const int nb = std::min<int32_t>(kSampleWidth, n_p - b0);
-    st = run_sample_batch(h, nb, p_host + b0, rtol, max_outer, iters_host + b0, relres_host + b0);
+    st = run_sample_batch(h, nb, ps.data() + b0, rtol, cap, race, it_s.data() + b0, rel_s.data() + b0);
     status_or |= h->ctl_host->status;
+    if (race)
+      for (int k = b0; k < b0 + nb; ++k)
+        if (rel_s[k] <= rtol) cap = std::min<int>(cap, it_s[k]);
+  }
+  for (int32_t k = 0; k < n_p; ++k) {
+    iters_host[order[k]] = it_s[k];
+    relres_host[order[k]] = rel_s[k];
   }
   h->last_kind = 1;
   osm_status st2 = apply_robin(h);  // back to the handle's own p

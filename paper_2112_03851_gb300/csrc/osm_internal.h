@@ -16,8 +16,9 @@ namespace osm {
 constexpr int kSliceRows = 32;
 constexpr int kTileRows = 256;
 constexpr int kTileSlices = kTileRows / kSliceRows;
-// Tiles per block of the FP32 CG update (all of one subdomain).
+// Tiles per block of the CG update (all of one subdomain): FP32 and FP64.
 constexpr int kUpdGroup = 8;
+constexpr int kUpdGroup64 = 2;
 // Threads of the one-block stop-test finaliser.
 constexpr int kResFinThreads = 1024;
 // SELL row widths are padded to a multiple of 4 so that every lane can load
@@ -157,7 +158,7 @@ struct DevCtl {
   int32_t n_active;       // subdomains still iterating
   int32_t status;         // OR of subdomain statuses seen in this solve
   int32_t total_inner;    // batched CG steps summed over the Schwarz iterations
-  int32_t pad0;
+  int32_t race;           // batched p evaluation: stop every candidate when the first converges
   double relres;          // last stop-test value
   double tau2_outer;      // mixed mode: FP64 local tolerance^2 that skips a correction
   unsigned long long t_start_ns;  // %globaltimer at the first kernel of the call
@@ -178,6 +179,8 @@ struct DevProblem {
   int32_t c16_64, c16_32;     // 1: the FP64 / FP32 SpMVs read cols16 (chosen by the autotuner)
   const int64_t* ub_tile0;    // first tile of each FP32-update block (kUpdGroup tiles, one subdomain)
   int64_t n_ublocks;
+  const int64_t* ub64_tile0;  // ... of each FP64-update block (kUpdGroup64 tiles)
+  int64_t n_ublocks64;
   double* vals;
   const int32_t* tile_sub;
   const int64_t* sub_tile0;   // n_sub + 1
@@ -212,8 +215,9 @@ struct DevProblem {
   int64_t n_nodes;
   const int32_t *cp_ptr, *cp_idx;
   double* phi;          // internal full-grid output
-  double* rpart;        // residual partials (per block)
-  double* rpart2;
+  double* rpart;        // stop-test partials of ||r||^2 (per residual block)
+  double* rpart2;       // ... of ||f||^2 (written once per solve by k_load_nodes)
+  double* fg;           // assembled load per node (full grid), set per solve
   int64_t n_rblocks;
   double* hist;         // residual history (max_outer)
   // instances
@@ -300,6 +304,8 @@ cudaError_t launch_cg_iteration(const DevProblem& d, cudaStream_t s, unsigned lo
 // and the state that makes it run on every subdomain (profiling only).
 cudaError_t launch_cg_spmv_alone(const DevProblem& d, int fp32, cudaStream_t s);
 cudaError_t launch_profile_state(const DevProblem& d, cudaStream_t s);
+// Assembled nodal load and ||f||^2 partials for the stop test (once per solve).
+cudaError_t launch_load_nodes(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_cg_iteration32(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
 cudaError_t launch_cg_init_mixed(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
 cudaError_t launch_mixed_correct(const DevProblem& d, cudaStream_t s);

@@ -148,33 +148,6 @@ __global__ void __launch_bounds__(kTileRows) k_cg_spmv(DevProblem d, CgVec<T> v)
   if (threadIdx.x == 0) d.part0[tile] = out[0];
 }
 
-// x += alpha p, r -= alpha q, z = D^-1 r, and the tile partials of r.z and
-// ||r||^2 (k_fin_beta turns them into rho, the stop test and beta).
-template <class T>
-__global__ void __launch_bounds__(kTileRows) k_cg_update(DevProblem d, CgVec<T> v) {
-  __shared__ double sm[2][kTileSlices];
-  const int64_t tile = blockIdx.x;
-  const int s = d.tile_sub[tile];
-  if (!d.st.active[s]) return;
-  const int64_t row = tile * kTileRows + threadIdx.x;
-  const T alpha = (T)d.st.alpha[s];
-  const T sc = sizeof(T) == 4 ? (T)d.st.sc[s] : T(1);
-  const T pr = v.p[row], xr = v.x[row], qr = v.q[row], rr0 = v.r[row], di = v.dinv[row];
-  v.x[row] = fma(alpha, pr, xr);
-  const T r = fma(-alpha, qr, rr0);
-  const T z = di * r;
-  v.r[row] = r;
-  v.z[row] = z;
-  const T rs = r * sc;
-  T vv[2] = {rs * (z * sc), rs * rs};
-  double out[2];
-  tile_dots<T, 2, kTileSlices>(vv, sizeof(T) == 4 ? d.st.isc2[s] : 1.0, sm, out);
-  if (threadIdx.x == 0) {
-    d.part1[tile] = out[0];
-    d.part2[tile] = out[1];
-  }
-}
-
 // Per-subdomain finalisers: one warp per subdomain adds the subdomain's tile
 // partials in a fixed order and updates its CG scalars, so the big kernels
 // carry no fences or atomics.  Launched with fin_blocks() blocks.
@@ -224,31 +197,11 @@ __global__ void k_fin_init(DevProblem d, int mixed, unsigned long long cond, int
   }
 }
 
-// alpha = rho / (p.q), or a breakdown stop of the subdomain.
-__global__ void k_fin_alpha(DevProblem d) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.x * kTileSlices + warp;
-  if (s >= d.n_sub || !d.st.active[s]) return;
-  const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
-  const double pq = warp_sum_parts(d.part0, t0, nt);
-  if (lane == 0) {
-    if (!(pq > 0.0) || !isfinite(pq)) {
-      d.st.alpha[s] = 0.0;
-      d.st.status[s] |= 2;
-      atomicOr(&d.ctl->status, 2);
-      d.st.active[s] = 0;
-      atomicSub(&d.ctl->n_active, 1);
-    } else {
-      d.st.alpha[s] = d.st.rho[s] / pq;
-    }
-  }
-}
-
 // rho = r.z, the stop test ||r|| <= tau ||b|| (or the iteration cap), beta;
 // the last block counts the step and sets the inner loop condition.
-// check_pq (three-kernel FP32 step, no k_fin_alpha): a subdomain whose p.q
-// partials (still in part0) sum to <= 0 stops with a breakdown.
-__global__ void k_fin_beta(DevProblem d, unsigned long long cond, int use_cond, int check_pq) {
+// A subdomain whose p.q partials (still in part0; k_cg_update_a left its
+// iterate alone) sum to <= 0 stops with a breakdown.
+__global__ void k_fin_beta(DevProblem d, unsigned long long cond, int use_cond) {
   __shared__ bool flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int s = blockIdx.x * kTileSlices + warp;
@@ -256,7 +209,7 @@ __global__ void k_fin_beta(DevProblem d, unsigned long long cond, int use_cond, 
     const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
     const double rz = warp_sum_parts(d.part1, t0, nt);
     const double rr = warp_sum_parts(d.part2, t0, nt);
-    const double pq = check_pq ? warp_sum_parts(d.part0, t0, nt) : 1.0;
+    const double pq = warp_sum_parts(d.part0, t0, nt);
     if (lane == 0) {
       const int it = d.st.iters[s] + 1;
       d.st.iters[s] = it;
@@ -303,7 +256,7 @@ __global__ void __launch_bounds__(kTileRows) k_cg_direction(DevProblem d, CgVec<
 //   p = z + beta p,   q = A p = t + beta q   (first step, beta = 0: p = z, q = t)
 // and alpha = rho / (p.q) is formed inside the update kernel (every block
 // of a subdomain adds the subdomain's p.q partials in the same fixed order),
-// so k_cg_direction and k_fin_alpha drop out.  Same vector traffic as the
+// so k_cg_direction and a separate alpha kernel drop out.  Same vector traffic as the
 // five-kernel step, two launches and one pass over the vectors fewer.
 template <int RPL, bool C16>
 __global__ void __launch_bounds__(kTileRows) k_cg_spmv_dir32(DevProblem d) {
@@ -339,51 +292,62 @@ __global__ void __launch_bounds__(kTileRows) k_cg_spmv_dir32(DevProblem d) {
 // alpha = rho / (p.q) (a breakdown, p.q <= 0, leaves the iterate alone and
 // k_fin_beta stops the subdomain), x += alpha p, r -= alpha q, z = D^-1 r,
 // and the tile partials of r.z and ||r||^2.  A block covers up to
-// kUpdGroup consecutive tiles of one subdomain (d.ub_tile0): alpha is formed
-// once per block, and every thread issues the loads of all its rows before
-// it waits for alpha, so the launch is about one wave of long-lived blocks
-// instead of many waves of blocks that each wait on alpha's L2 round trips.
-__global__ void __launch_bounds__(kTileRows) k_cg_update_a32(DevProblem d) {
-  __shared__ double sm[kUpdGroup][2][kTileSlices];
-  __shared__ float s_alpha;
+// G consecutive tiles of one subdomain (d.ub_tile0 / d.ub64_tile0; FP32: 8,
+// FP64: 2, which keeps its registers, and so its occupancy, up): alpha is formed
+// once per block (the same expression and summation order in every block,
+// so the step is bit-identical to a separate alpha kernel), and every thread
+// issues the loads of all its rows before it waits for alpha, so the launch
+// is a couple of waves of long-lived blocks instead of many waves of blocks
+// that each wait on alpha's L2 round trips.  T = double: the FP64 CG (FP64
+// dots); T = float: the mixed form's inner CG (scaled FP32 dots).
+template <class T, int G>
+__global__ void __launch_bounds__(kTileRows) k_cg_update_a(DevProblem d, CgVec<T> v) {
+  __shared__ double sm[G][2][kTileSlices];
+  __shared__ T s_alpha;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t t0 = d.ub_tile0[blockIdx.x];
+  const int64_t t0 = (G == kUpdGroup ? d.ub_tile0 : d.ub64_tile0)[blockIdx.x];
   const int s = d.tile_sub[t0];
   if (!d.st.active[s]) return;
   const int64_t ts0 = d.sub_tile0[s];
-  const int nt = (int)min((int64_t)kUpdGroup, d.sub_tile0[s + 1] - t0);
-  float pr[kUpdGroup], xr[kUpdGroup], qr[kUpdGroup], rr0[kUpdGroup], di[kUpdGroup];
+  const int nt = (int)min((int64_t)G, d.sub_tile0[s + 1] - t0);
+  T pr[G], xr[G], qr[G], rr0[G], di[G];
 #pragma unroll
-  for (int j = 0; j < kUpdGroup; ++j) {
+  for (int j = 0; j < G; ++j) {
     if (j < nt) {
       const int64_t row = (t0 + j) * kTileRows + threadIdx.x;
-      pr[j] = d.p32[row];
-      xr[j] = d.x32[row];
-      qr[j] = d.q32[row];
-      rr0[j] = d.r32[row];
-      di[j] = d.dinv32[row];
+      pr[j] = v.p[row];
+      xr[j] = v.x[row];
+      qr[j] = v.q[row];
+      rr0[j] = v.r[row];
+      di[j] = v.dinv[row];
     }
   }
   if (warp == 0) {
     const double pq = warp_sum_parts(d.part0, ts0, d.sub_tile0[s + 1] - ts0);
-    if (lane == 0) s_alpha = (pq > 0.0 && isfinite(pq)) ? (float)(d.st.rho[s] / pq) : 0.f;
+    if (lane == 0) s_alpha = (pq > 0.0 && isfinite(pq)) ? (T)(d.st.rho[s] / pq) : T(0);
   }
   __syncthreads();
-  const float alpha = s_alpha, sc = d.st.sc[s];
-  const double isc2 = d.st.isc2[s];
+  const T alpha = s_alpha;
+  const T sc = sizeof(T) == 4 ? (T)d.st.sc[s] : T(1);
+  const double isc2 = sizeof(T) == 4 ? d.st.isc2[s] : 1.0;
 #pragma unroll
-  for (int j = 0; j < kUpdGroup; ++j) {
-    float a = 0.f, b = 0.f;
+  for (int j = 0; j < G; ++j) {
+    T a = T(0), b = T(0);
     if (j < nt) {
       const int64_t row = (t0 + j) * kTileRows + threadIdx.x;
-      d.x32[row] = fmaf(alpha, pr[j], xr[j]);
-      const float r = fmaf(-alpha, qr[j], rr0[j]);
-      const float z = di[j] * r;
-      d.r32[row] = r;
-      d.z32[row] = z;
-      const float rs = r * sc;
-      a = rs * (z * sc);
-      b = rs * rs;
+      v.x[row] = fma(alpha, pr[j], xr[j]);
+      const T r = fma(-alpha, qr[j], rr0[j]);
+      const T z = di[j] * r;
+      v.r[row] = r;
+      v.z[row] = z;
+      if constexpr (sizeof(T) == 8) {   // FP64: no scaling (FP64 multiplies are scarce)
+        a = r * z;
+        b = r * r;
+      } else {
+        const T rs = r * sc;
+        a = rs * (z * sc);
+        b = rs * rs;
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -398,10 +362,10 @@ __global__ void __launch_bounds__(kTileRows) k_cg_update_a32(DevProblem d) {
   __syncthreads();
   if (threadIdx.x < 2 * nt) {
     const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
-    double v = 0.0;
+    double acc = 0.0;
 #pragma unroll
-    for (int w = 0; w < kTileSlices; ++w) v += sm[j][which][w];
-    (which ? d.part2 : d.part1)[t0 + j] = v;
+    for (int w = 0; w < kTileSlices; ++w) acc += sm[j][which][w];
+    (which ? d.part2 : d.part1)[t0 + j] = acc;
   }
 }
 
@@ -571,27 +535,38 @@ __global__ void k_face_correct(DevProblem d, const double* __restrict__ x, doubl
 // the per-block partials of ||r||^2 and ||f||^2 (no tickets: the single-block
 // k_residual_fin adds them).
 __global__ void __launch_bounds__(256) k_residual(DevProblem d) {
-  __shared__ double sm[2][kTileSlices];
+  __shared__ double sm[1][kTileSlices];
   const int b = blockIdx.x;
-  double v[2] = {0.0, 0.0};
+  double v[1] = {0.0};
   if (!d.inst_done[d.rblock_inst[b]]) {
     for (int64_t n = d.rblock_node0[b] + threadIdx.x; n < d.rblock_node0[b + 1]; n += blockDim.x) {
       const int32_t c0 = d.cp_ptr[n], c1 = d.cp_ptr[n + 1];
-      double fg = 0.0, ku = 0.0;
-      for (int32_t c = c0; c < c1; ++c) {
-        fg += d.f[d.cp_idx[c]];
-        ku += d.y[d.cp_idx[c]];
-      }
-      const double r = fg - ku;
+      double ku = 0.0;
+      for (int32_t c = c0; c < c1; ++c) ku += d.y[d.cp_idx[c]];
+      const double r = d.fg[n] - ku;
       v[0] += r * r;
-      v[1] += fg * fg;
     }
   }
-  block_sum<2>(v, sm);
-  if (threadIdx.x == 0) {
-    d.rpart[b] = v[0];
-    d.rpart2[b] = v[1];
+  block_sum<1>(v, sm);
+  if (threadIdx.x == 0) d.rpart[b] = v[0];
+}
+
+// Start of a solve: the assembled load f_n = sum over the copies of each
+// node (constant during the solve) and the block partials of ||f||^2 that
+// every stop test divides by.
+__global__ void __launch_bounds__(256) k_load_nodes(DevProblem d) {
+  __shared__ double sm[1][kTileSlices];
+  const int b = blockIdx.x;
+  double v[1] = {0.0};
+  for (int64_t n = d.rblock_node0[b] + threadIdx.x; n < d.rblock_node0[b + 1]; n += blockDim.x) {
+    const int32_t c0 = d.cp_ptr[n], c1 = d.cp_ptr[n + 1];
+    double fg = 0.0;
+    for (int32_t c = c0; c < c1; ++c) fg += d.f[d.cp_idx[c]];
+    d.fg[n] = fg;
+    v[0] += fg * fg;
   }
+  block_sum<1>(v, sm);
+  if (threadIdx.x == 0) d.rpart2[b] = v[0];
 }
 
 // Stop test, step 3 (one block): per instance, ||r|| / ||f|| from its block
@@ -704,17 +679,17 @@ cudaError_t launch_cg_iteration(const DevProblem& d, cudaStream_t s, unsigned lo
     if (d.rpl64 == 2) k_cg_spmv<double, 2, false><<<(unsigned)d.n_tiles, kTileRows / 2, 0, s>>>(d, v);
     else k_cg_spmv<double, 1, false><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
   }
-  k_fin_alpha<<<fin_blocks(d), kTileRows, 0, s>>>(d);
-  k_cg_update<double><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
-  k_fin_beta<<<fin_blocks(d), kTileRows, 0, s>>>(d, cond, use_cond, 0);
+  k_cg_update_a<double, kUpdGroup64><<<(unsigned)d.n_ublocks64, kTileRows, 0, s>>>(d, v);
+  k_fin_beta<<<fin_blocks(d), kTileRows, 0, s>>>(d, cond, use_cond);
   k_cg_direction<double><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_iteration32(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
   OSM_LAUNCH_RPL(d.rpl32, d.c16_32, k_cg_spmv_dir32, s, d);
-  k_cg_update_a32<<<(unsigned)d.n_ublocks, kTileRows, 0, s>>>(d);
-  k_fin_beta<<<fin_blocks(d), kTileRows, 0, s>>>(d, cond, use_cond, 1);
+  const CgVec<float> v{d.x32, d.r32, d.z32, d.p32, d.q32, d.dinv32, d.vals32};
+  k_cg_update_a<float, kUpdGroup><<<(unsigned)d.n_ublocks, kTileRows, 0, s>>>(d, v);
+  k_fin_beta<<<fin_blocks(d), kTileRows, 0, s>>>(d, cond, use_cond);
   return cudaGetLastError();
 }
 
@@ -779,6 +754,11 @@ cudaError_t launch_residual(const DevProblem& d, cudaStream_t s, unsigned long l
   if (d.n_irow) k_face_correct<<<blocks_for(d.n_irow, 256), 256, 0, s>>>(d, d.w, d.y);
   k_residual<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
   k_residual_fin<<<1, kResFinThreads, 0, s>>>(d, cond, use_cond);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_nodes(const DevProblem& d, cudaStream_t s) {
+  k_load_nodes<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
   return cudaGetLastError();
 }
 

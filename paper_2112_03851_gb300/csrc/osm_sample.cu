@@ -189,12 +189,18 @@ __global__ void __launch_bounds__(kTileRows) k_mp_cg_spmv(DevProblem d, DevSampl
   const double pk = m.psamp[k];
   const T sc = sizeof(T) == 4 ? (T)m.sc[sk] : T(1);
   MpDot<T> pq;
-  for (int rl = 0; rl < kSliceRows; ++rl) {
-    const int64_t row = slice * kSliceRows + rl;
-    const T q = mp_row<T>(d, m, off, rl, w, Xs, v.pd, row, true, pk, k);
-    const int64_t idx = row * W + k;
-    v.q[idx] = q;
-    pq.add(v.pd[idx], q, sc);
+  // only the candidates still iterating on this subdomain gather and compute:
+  // a finished candidate's lane requests no sectors of the candidate rows
+  // (the host sorts candidates by p, so the lanes still running tend to be
+  // neighbours and share sectors)
+  if (act) {
+    for (int rl = 0; rl < kSliceRows; ++rl) {
+      const int64_t row = slice * kSliceRows + rl;
+      const T q = mp_row<T>(d, m, off, rl, w, Xs, v.pd, row, true, pk, k);
+      const int64_t idx = row * W + k;
+      v.q[idx] = q;
+      pq.add(v.pd[idx], q, sc);
+    }
   }
   double acc[1] = {(double)pq.acc * (sizeof(T) == 4 ? m.isc2[sk] : 1.0)};
   lane_block_sum<1>(acc, sm);
@@ -481,11 +487,16 @@ __global__ void __launch_bounds__(256) k_mp_residual(DevProblem d, DevSample m, 
     }
     const double rel = ff > 0.0 ? sqrt(rr / ff) : sqrt(rr);
     const int n_outer = d.ctl->n_outer + 1;
-    if (!m.done[k]) {
+    const bool live = !m.done[k];
+    if (live) {
       m.relres[k] = rel;
       m.outer_iters[k] = n_outer;
       if (rel <= d.ctl->rtol || !isfinite(rel) || n_outer >= d.ctl->max_outer) m.done[k] = 1;
     }
+    // race: once a candidate reaches rtol, no candidate still running can
+    // need fewer iterations, so all stop here (each keeps this residual)
+    const unsigned won = __ballot_sync(0xffffffffu, live && rel <= d.ctl->rtol);
+    if (d.ctl->race && won) m.done[k] = 1;
     const unsigned running = __ballot_sync(0xffffffffu, !m.done[k]);
     if (k == 0) {
       d.ctl->n_outer = n_outer;

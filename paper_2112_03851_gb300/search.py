@@ -157,19 +157,27 @@ def optimise_fourier(kind="oo0_sym", kmin=0.0174, kmax=1.915, seed=0, max_iter=7
 
 # ------------------------------------------------- Schwarz iteration cost --
 
-def schwarz_iterations_cost(solver, rtol=1e-8, max_outer=400):
-    """Cost of log p: Schwarz iterations to rtol (plus the final residual as
-    a tie-break below one iteration), one batched GPU run per generation."""
+def schwarz_iterations_cost(solver, rtol=1e-8, max_outer=400, race=True):
+    """Cost of log p: Schwarz iterations to rtol, one batched GPU run per
+    generation.  A converged candidate costs its count plus its residual
+    (a tie-break below half an iteration); one that was stopped before
+    converging (at the cap, or, with race, when the generation's first
+    candidate converged) costs its count plus 1/2 plus log10 of how far its
+    residual still is from rtol, so the ranking among those follows the
+    residual they reached."""
 
     def batch(X):
         ps = np.exp(np.asarray(X, dtype=np.float64)[:, 0])
-        iters, rel, _ = solver.sample_p(ps, rtol=rtol, max_outer=max_outer)
-        return iters.astype(np.float64) + np.minimum(rel / rtol, 1.0) * 0.5
+        iters, rel, _ = solver.sample_p(ps, rtol=rtol, max_outer=max_outer, race=race)
+        conv = rel <= rtol
+        cost = iters.astype(np.float64) + 0.5 * np.where(conv, rel / rtol, 1.0)
+        return cost + np.where(conv, 0.0, np.log10(np.maximum(rel / rtol, 1.0)))
     return batch
 
 
-def search_p(solver, p0=10.0, sigma0=1.0, popsize=25, generations=10, rtol=1e-8, max_outer=400, seed=0):
+def search_p(solver, p0=10.0, sigma0=1.0, popsize=25, generations=10, rtol=1e-8, max_outer=400, seed=0,
+             race=True):
     """CMA-ES over log p with the measured Schwarz iteration count as cost."""
-    res = cma_es(schwarz_iterations_cost(solver, rtol, max_outer), np.array([math.log(p0)]), sigma0,
+    res = cma_es(schwarz_iterations_cost(solver, rtol, max_outer, race), np.array([math.log(p0)]), sigma0,
                  popsize=popsize, max_iter=generations, tol=0.5, seed=seed)
     return float(np.exp(res.x[0])), res

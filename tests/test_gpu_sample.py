@@ -119,3 +119,29 @@ def test_cma_es_search_with_batched_evaluation(osm):
     it_s, rel_s, best_s = sol.sample_p(ps, rtol=1e-8, max_outer=400)
     assert rel[0] <= 1e-8 and iters[0] <= it_s[best_s]
     assert res.evaluations == 16 * res.iterations
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_race_mode_finds_the_same_winner(osm, prec):
+    """OSM_SAMPLE_RACE stops a batch at its first convergence: the winner
+    (and every candidate converging at the same iteration) keeps exactly its
+    full-run iteration count and residual; the others stop at or before the
+    winner's count with a residual above rtol.  Across batches of 32, a later
+    batch is capped at the best count so far."""
+    prob = gen.sphere_problem(8, 2, 4.0)
+    sol = osm.Solver.from_problem(prob, prec=prec, inner_rtol=1e-10, mixed_inner_rtol=0.3, max_outer=400)
+    ps = gen.log_uniform_p(21, 40, 0.5, 40.0)
+    it_full, rel_full, best_full = sol.sample_p(ps, rtol=1e-8, max_outer=400)
+    it_race, rel_race, best_race = sol.sample_p(ps, rtol=1e-8, max_outer=400, race=True)
+    assert best_race == best_full
+    n_star = it_full[best_full]
+    for k in range(len(ps)):
+        if rel_race[k] <= 1e-8:
+            assert it_race[k] == it_full[k] == n_star and rel_race[k] == rel_full[k], k
+        else:
+            assert it_race[k] <= n_star, k
+    # unknown flags are rejected before anything runs
+    one, it1, rel1, b1 = np.ones(1), np.zeros(1, dtype=np.int32), np.zeros(1), np.zeros(1, dtype=np.int32)
+    st = osm.load().osm_sample_p_ex(sol._h, 1, osm._lib._ptr(one), 1e-8, 10, 4, osm._lib._ptr(it1),
+                                    osm._lib._ptr(rel1), osm._lib._ptr(b1))
+    assert st == osm._lib.OSM_E_ARG
