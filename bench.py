@@ -93,22 +93,43 @@ def _peaks():
         return FALLBACK_HBM, "fallback"
 
 
+def _definitions(text):
+    """name -> source text of every function defined at column 0 (from its
+    template line to the closing brace at column 0)."""
+    import re
+    lines = text.split("\n")
+    out = {}
+    for i, ln in enumerate(lines):
+        m = re.match(r"(?:__global__|__device__)[^(]*?\b(\w+)\(", re.sub(r"__launch_bounds__\([^)]*\)", "", ln))
+        if not m:
+            continue
+        start = i
+        while start > 0 and lines[start - 1].startswith("template"):
+            start -= 1
+        end = next(j for j in range(i, len(lines)) if lines[j] == "}")
+        out[m.group(1)] = "\n".join(lines[start:end + 1])
+    return out
+
+
 def _kernel_hash(kernel):
-    """Hash of one kernel's source: its definition in osm_kernels.cu (from its
-    template line to the closing brace at column 0) plus the device helpers
-    (osm_device.cuh) and the data layout (osm_internal.h) it uses."""
+    """Hash of one kernel's source: its definition and, transitively, the
+    device helpers it calls (osm_kernels.cu, osm_device.cuh)."""
+    import re
     csrc = os.path.join(ROOT, "paper_2112_03851_gb300", "csrc")
+    defs = {}
+    for name in ("osm_device.cuh", "osm_kernels.cu"):
+        with open(os.path.join(csrc, name)) as f:
+            defs.update(_definitions(f.read()))
+    seen, todo = [], [kernel]
+    while todo:
+        k = todo.pop()
+        if k in seen or k not in defs:
+            continue
+        seen.append(k)
+        todo += [n for n in re.findall(r"\b(\w+)\s*[<(]", defs[k]) if n in defs and n != k]
     h = hashlib.sha256()
-    with open(os.path.join(csrc, "osm_kernels.cu")) as f:
-        lines = f.read().split("\n")
-    start = next(i for i, ln in enumerate(lines) if "__global__" in ln and f" {kernel}(" in ln)
-    while start > 0 and lines[start - 1].startswith("template"):
-        start -= 1
-    end = next(i for i in range(start, len(lines)) if lines[i] == "}")
-    h.update("\n".join(lines[start:end + 1]).encode())
-    for name in ("osm_device.cuh", "osm_internal.h"):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+    for k in sorted(seen):
+        h.update(defs[k].encode())
     return h.hexdigest()[:16]
 
 
@@ -624,8 +645,9 @@ def profile_sample(args):
     import paper_2112_03851_gb300 as pkg
     torch.cuda.set_device(0)
     prob = gen.workload(args.workload or WORKLOAD)
-    sol = pkg.Solver.from_problem(prob, p=P_ROBIN, inner_rtol=INNER_RTOL, max_outer=5000,
-                                  use_graph=0 if args.launch == "host" else 1)
+    prec = "fp64" if args.prec == "both" else args.prec
+    sol = pkg.Solver.from_problem(prob, p=P_ROBIN, inner_rtol=INNER_RTOL, max_outer=5000, prec=prec,
+                                  mixed_inner_rtol=MIXED_INNER_RTOL, use_graph=0 if args.launch == "host" else 1)
     ps = gen.log_uniform_p(0, 32, 0.5, 200.0)
     iters, rel, best = sol.sample_p(ps, rtol=RTOL, max_outer=2)
     print(json.dumps({"profile_sample": args.workload or WORKLOAD, "relres_min": float(rel.min()),

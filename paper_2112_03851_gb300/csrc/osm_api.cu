@@ -149,6 +149,7 @@ osm_status upload_problem(osm_ctx* h) {
   DevSubState& st = d.st;
   for (double** v : {&st.rho, &st.alpha, &st.beta, &st.bb, &st.rr}) OSM_CUDA(h, dalloc(h, v, ns));
   for (int32_t** v : {&st.active, &st.iters, &st.status}) OSM_CUDA(h, dalloc(h, v, ns));
+  OSM_CUDA(h, dalloc(h, &st.ucnt, ns));
   OSM_CUDA(h, dalloc(h, &st.sc, ns));
   OSM_CUDA(h, dalloc(h, &st.isc2, ns));
   for (double** v : {&d.part0, &d.part1, &d.part2}) OSM_CUDA(h, dalloc(h, v, hp.n_tiles));

@@ -39,6 +39,40 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double (*sm)[SW]) {
   }
 }
 
+// Sum NV doubles over the NT threads of a block with about one FP64 add per
+// value: the values are staged in shared memory, 8 threads per value add
+// interleaved eighths in a fixed order, and thread 0 adds the 8 partials.
+// A warp butterfly costs five FP64 adds per lane and value, and FP64 is the
+// scarce pipe on this GPU: in FP64-bound kernels (the FP64 SpMVs and CG
+// update) the butterflies took a large share of it.  Result in thread 0.
+template <int NV, int NT>
+__device__ __forceinline__ void block_sum_d(double (&v)[NV], double (*sm)[NT]) {
+  static_assert(NT % 8 == 0 && NV * 8 <= NT, "block too small for the staged sum");
+  constexpr int kChunk = NT / 8;
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) sm[k][t] = v[k];
+  __syncthreads();
+  double part = 0.0;
+  if (t < NV * 8) {
+    const int k = t >> 3, c = t & 7;
+#pragma unroll 8
+    for (int i = 0; i < kChunk; ++i) part += sm[k][i * 8 + c];
+  }
+  __syncthreads();
+  if (t < NV * 8) sm[t >> 3][t & 7] = part;
+  __syncthreads();
+  if (t == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double s = 0.0;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) s += sm[k][c];
+      v[k] = s;
+    }
+  }
+}
+
 // Sum of part[t0 .. t0+nt) in a fixed order by one warp (all lanes get it).
 // Four independent loads per lane per step keep several L2 requests in flight.
 __device__ __forceinline__ double warp_sum_parts(const double* part, int64_t t0, int64_t nt) {

@@ -142,6 +142,7 @@ struct DevSubState {
   int32_t* active;  // 1 while the subdomain's CG runs
   int32_t* iters;   // CG iterations of the current solve
   int32_t* status;  // 0 ok, 1 cap reached, 2 breakdown
+  unsigned* ucnt;   // per-subdomain ticket of the CG update's blocks (reset by the last)
   float* sc;        // FP32 inner solve: power of two applied to both factors
                     // of every FP32 dot product (keeps r*r out of underflow)
   double* isc2;     // 1 / sc^2, undoes that scaling on the warp partials

@@ -69,7 +69,7 @@ __global__ void k_rhs_gather(DevProblem d) {
 // tile partials of ||r||^2, ||b||^2 and r.z (finalised by k_fin_init).
 template <int RPL, bool C16>
 __global__ void __launch_bounds__(kTileRows) k_cg_init(DevProblem d) {
-  __shared__ double sm[3][kTileSlices];
+  __shared__ double sm[3][kTileRows / RPL];
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
   const int64_t t0 = d.sub_tile0[s];
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kTileRows) k_cg_init(DevProblem d) {
     v[1] += b * b;
     v[2] += r * z;
   }
-  block_sum<3, kTileSlices / RPL>(v, sm);
+  block_sum_d<3, kTileRows / RPL>(v, sm);
   if (threadIdx.x == 0) {
     d.part0[tile] = v[0];
     d.part1[tile] = v[1];
@@ -128,7 +128,7 @@ __device__ __forceinline__ void tile_dots(T (&v)[NV], double isc2, double (*sm)[
 // the FP64 solve, float for the mixed-precision inner solve).
 template <class T, int RPL, bool C16>
 __global__ void __launch_bounds__(kTileRows) k_cg_spmv(DevProblem d, CgVec<T> v) {
-  __shared__ double sm[1][kTileSlices];
+  __shared__ double sm[1][kTileRows / RPL];
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
   if (!d.st.active[s]) return;
@@ -143,9 +143,9 @@ __global__ void __launch_bounds__(kTileRows) k_cg_spmv(DevProblem d, CgVec<T> v)
     v.q[row[k]] = q[k];
     vv[0] = fma(v.p[row[k]] * sc, q[k] * sc, vv[0]);
   }
-  double out[1];
-  tile_dots<T, 1, kTileSlices / RPL>(vv, sizeof(T) == 4 ? d.st.isc2[s] : 1.0, sm, out);
-  if (threadIdx.x == 0) d.part0[tile] = out[0];
+  double out[1] = {(double)vv[0]};
+  block_sum_d<1, kTileRows / RPL>(out, sm);
+  if (threadIdx.x == 0) d.part0[tile] = out[0] * (sizeof(T) == 4 ? d.st.isc2[s] : 1.0);
 }
 
 // Per-subdomain finalisers: one warp per subdomain adds the subdomain's tile
@@ -197,48 +197,53 @@ __global__ void k_fin_init(DevProblem d, int mixed, unsigned long long cond, int
   }
 }
 
-// rho = r.z, the stop test ||r|| <= tau ||b|| (or the iteration cap), beta;
-// the last block counts the step and sets the inner loop condition.
-// A subdomain whose p.q partials (still in part0; k_cg_update_a left its
+// End of a CG step for subdomain s, by one warp (the finishing block of
+// k_cg_update_a): rho = r.z, the stop test ||r|| <= tau ||b|| (or the
+// iteration cap), beta, from the tile partials in a fixed order.  A
+// subdomain whose p.q partials (still in part0; k_cg_update_a left its
 // iterate alone) sum to <= 0 stops with a breakdown.
-__global__ void k_fin_beta(DevProblem d, unsigned long long cond, int use_cond) {
-  __shared__ bool flag;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int s = blockIdx.x * kTileSlices + warp;
-  if (s < d.n_sub && d.st.active[s]) {
-    const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
-    const double rz = warp_sum_parts(d.part1, t0, nt);
-    const double rr = warp_sum_parts(d.part2, t0, nt);
-    const double pq = warp_sum_parts(d.part0, t0, nt);
-    if (lane == 0) {
-      const int it = d.st.iters[s] + 1;
-      d.st.iters[s] = it;
-      d.st.rr[s] = rr;
-      if (!(pq > 0.0) || !isfinite(pq)) {
-        d.st.status[s] |= 2;
-        atomicOr(&d.ctl->status, 2);
-        d.st.active[s] = 0;
-        atomicSub(&d.ctl->n_active, 1);
-      } else if (rr <= d.ctl->tau2 * d.st.bb[s]) {
-        d.st.active[s] = 0;
-        atomicSub(&d.ctl->n_active, 1);
-      } else if (it >= d.ctl->max_inner) {
-        d.st.active[s] = 0;
-        d.st.status[s] |= 1;
-        atomicOr(&d.ctl->status, 1);
-        atomicSub(&d.ctl->n_active, 1);
-      }
-      d.st.beta[s] = rz / d.st.rho[s];
-      d.st.rho[s] = rz;
+__device__ __forceinline__ void cg_step_finish(DevProblem& d, int s, int lane) {
+  const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
+  const double rz = warp_sum_parts(d.part1, t0, nt);
+  const double rr = warp_sum_parts(d.part2, t0, nt);
+  const double pq = warp_sum_parts(d.part0, t0, nt);
+  if (lane == 0) {
+    const int it = d.st.iters[s] + 1;
+    d.st.iters[s] = it;
+    d.st.rr[s] = rr;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      d.st.status[s] |= 2;
+      atomicOr(&d.ctl->status, 2);
+      d.st.active[s] = 0;
+      atomicSub(&d.ctl->n_active, 1);
+    } else if (rr <= d.ctl->tau2 * d.st.bb[s]) {
+      d.st.active[s] = 0;
+      atomicSub(&d.ctl->n_active, 1);
+    } else if (it >= d.ctl->max_inner) {
+      d.st.active[s] = 0;
+      d.st.status[s] |= 1;
+      atomicOr(&d.ctl->status, 1);
+      atomicSub(&d.ctl->n_active, 1);
     }
+    d.st.beta[s] = rz / d.st.rho[s];
+    d.st.rho[s] = rz;
   }
-  if (last_block(&d.ctl->gcnt_b, gridDim.x, &flag) && threadIdx.x == 0) {
-    const int n_inner = d.ctl->n_inner + 1;
-    d.ctl->n_inner = n_inner;
-    d.ctl->total_inner += 1;
-    const bool more = d.ctl->n_active > 0 && n_inner <= d.ctl->max_inner && !out_of_time(d.ctl);
-    if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
-  }
+}
+
+// Every subdomain arrives here once per CG step (its finishing block, or the
+// first block of an inactive one); the last of the n_sub arrivals counts the
+// step and sets the inner loop condition.  A ticket, not a wait.
+__device__ __forceinline__ void cg_step_arrive(DevProblem& d, unsigned long long cond, int use_cond) {
+  __threadfence();
+  const unsigned g = atomicAdd(&d.ctl->gcnt_b, 1u);
+  if (g != (unsigned)d.n_sub - 1u) return;
+  d.ctl->gcnt_b = 0u;
+  __threadfence();
+  const int n_inner = d.ctl->n_inner + 1;
+  d.ctl->n_inner = n_inner;
+  d.ctl->total_inner += 1;
+  const bool more = atomicAdd(&d.ctl->n_active, 0) > 0 && n_inner <= d.ctl->max_inner && !out_of_time(d.ctl);
+  if (use_cond) cudaGraphSetConditional(cond, more ? 1u : 0u);
 }
 
 // p = z + beta p for subdomains still iterating.
@@ -290,8 +295,10 @@ __global__ void __launch_bounds__(kTileRows) k_cg_spmv_dir32(DevProblem d) {
 }
 
 // alpha = rho / (p.q) (a breakdown, p.q <= 0, leaves the iterate alone and
-// k_fin_beta stops the subdomain), x += alpha p, r -= alpha q, z = D^-1 r,
-// and the tile partials of r.z and ||r||^2.  A block covers up to
+// the step's finish stops the subdomain), x += alpha p, r -= alpha q,
+// z = D^-1 r, and the tile partials of r.z and ||r||^2; the subdomain's last
+// block to finish then ends the step (cg_step_finish, cg_step_arrive).
+// A block covers up to
 // G consecutive tiles of one subdomain (d.ub_tile0 / d.ub64_tile0; FP32: 8,
 // FP64: 2, which keeps its registers, and so its occupancy, up): alpha is formed
 // once per block (the same expression and summation order in every block,
@@ -301,14 +308,20 @@ __global__ void __launch_bounds__(kTileRows) k_cg_spmv_dir32(DevProblem d) {
 // that each wait on alpha's L2 round trips.  T = double: the FP64 CG (FP64
 // dots); T = float: the mixed form's inner CG (scaled FP32 dots).
 template <class T, int G>
-__global__ void __launch_bounds__(kTileRows) k_cg_update_a(DevProblem d, CgVec<T> v) {
+__global__ void __launch_bounds__(kTileRows) k_cg_update_a(DevProblem d, CgVec<T> v, unsigned long long cond,
+                                                           int use_cond) {
   __shared__ double sm[G][2][kTileSlices];
+  __shared__ double sm64[sizeof(T) == 8 ? 2 * G : 1][sizeof(T) == 8 ? kTileRows : 1];
   __shared__ T s_alpha;
+  __shared__ bool s_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t t0 = (G == kUpdGroup ? d.ub_tile0 : d.ub64_tile0)[blockIdx.x];
   const int s = d.tile_sub[t0];
-  if (!d.st.active[s]) return;
   const int64_t ts0 = d.sub_tile0[s];
+  if (!d.st.active[s]) {
+    if (t0 == ts0 && threadIdx.x == 0) cg_step_arrive(d, cond, use_cond);
+    return;
+  }
   const int nt = (int)min((int64_t)G, d.sub_tile0[s + 1] - t0);
   T pr[G], xr[G], qr[G], rr0[G], di[G];
 #pragma unroll
@@ -349,24 +362,64 @@ __global__ void __launch_bounds__(kTileRows) k_cg_update_a(DevProblem d, CgVec<T
         b = rs * rs;
       }
     }
+    if constexpr (sizeof(T) == 8) {
+      // staged in shared memory: about one FP64 add per value (block_sum_d)
+      sm64[2 * j][threadIdx.x] = a;
+      sm64[2 * j + 1][threadIdx.x] = b;
+    } else {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      b += __shfl_xor_sync(0xffffffffu, b, o);
-    }
-    if (lane == 0) {
-      sm[j][0][warp] = (double)a * isc2;
-      sm[j][1][warp] = (double)b * isc2;
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+      }
+      if (lane == 0) {
+        sm[j][0][warp] = (double)a * isc2;
+        sm[j][1][warp] = (double)b * isc2;
+      }
     }
   }
   __syncthreads();
-  if (threadIdx.x < 2 * nt) {
+  if constexpr (sizeof(T) == 8) {
+    // 8 threads per (tile, value) add interleaved eighths; then 8 partials each
+    double part = 0.0;
+    if (threadIdx.x < 16 * G) {
+      const int kv = threadIdx.x >> 3, c = threadIdx.x & 7;
+#pragma unroll 8
+      for (int i = 0; i < kTileRows / 8; ++i) part += sm64[kv][i * 8 + c];
+    }
+    __syncthreads();
+    if (threadIdx.x < 16 * G) sm64[threadIdx.x >> 3][threadIdx.x & 7] = part;
+    __syncthreads();
+    if (threadIdx.x < 2 * nt) {
+      double acc = 0.0;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) acc += sm64[threadIdx.x][c];
+      (threadIdx.x & 1 ? d.part2 : d.part1)[t0 + (threadIdx.x >> 1)] = acc;
+      __threadfence();   // each writer publishes its partial before the block's ticket
+    }
+  } else if (threadIdx.x < 2 * nt) {
     const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
     double acc = 0.0;
 #pragma unroll
     for (int w = 0; w < kTileSlices; ++w) acc += sm[j][which][w];
     (which ? d.part2 : d.part1)[t0 + j] = acc;
+    __threadfence();   // each writer publishes its partial before the block's ticket
   }
+  // the last block of the subdomain to get here finishes its CG step
+  // (replaces a separate finaliser launch per step)
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned nblk = (unsigned)((d.sub_tile0[s + 1] - ts0 + G - 1) / G);
+    const unsigned t = atomicAdd(&d.st.ucnt[s], 1u);
+    s_last = t == nblk - 1u;
+    if (s_last) d.st.ucnt[s] = 0u;
+  }
+  __syncthreads();
+  if (!s_last || warp != 0) return;
+  __threadfence();
+  cg_step_finish(d, s, lane);
+  if (lane == 0) cg_step_arrive(d, cond, use_cond);
 }
 
 // Profiling state: every subdomain active, beta = 1/2 (the full epilogue of
@@ -386,7 +439,7 @@ __global__ void k_profile_state(DevProblem d) {
 // ||b||^2 and r.z (k_fin_init decides which subdomains are corrected).
 template <int RPL, bool C16>
 __global__ void __launch_bounds__(kTileRows) k_cg_init_mixed(DevProblem d) {
-  __shared__ double sm[3][kTileSlices];
+  __shared__ double sm[3][kTileRows / RPL];
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
   const int64_t t0 = d.sub_tile0[s];
@@ -407,7 +460,7 @@ __global__ void __launch_bounds__(kTileRows) k_cg_init_mixed(DevProblem d) {
     vv[1] += b * b;
     vv[2] += (double)r * (double)z;
   }
-  block_sum<3, kTileSlices / RPL>(vv, sm);
+  block_sum_d<3, kTileRows / RPL>(vv, sm);
   if (threadIdx.x == 0) {
     d.part0[tile] = vv[0];
     d.part1[tile] = vv[1];
@@ -535,7 +588,7 @@ __global__ void k_face_correct(DevProblem d, const double* __restrict__ x, doubl
 // the per-block partials of ||r||^2 and ||f||^2 (no tickets: the single-block
 // k_residual_fin adds them).
 __global__ void __launch_bounds__(256) k_residual(DevProblem d) {
-  __shared__ double sm[1][kTileSlices];
+  __shared__ double sm[1][256];
   const int b = blockIdx.x;
   double v[1] = {0.0};
   if (!d.inst_done[d.rblock_inst[b]]) {
@@ -547,7 +600,7 @@ __global__ void __launch_bounds__(256) k_residual(DevProblem d) {
       v[0] += r * r;
     }
   }
-  block_sum<1>(v, sm);
+  block_sum_d<1, 256>(v, sm);
   if (threadIdx.x == 0) d.rpart[b] = v[0];
 }
 
@@ -555,7 +608,7 @@ __global__ void __launch_bounds__(256) k_residual(DevProblem d) {
 // node (constant during the solve) and the block partials of ||f||^2 that
 // every stop test divides by.
 __global__ void __launch_bounds__(256) k_load_nodes(DevProblem d) {
-  __shared__ double sm[1][kTileSlices];
+  __shared__ double sm[1][256];
   const int b = blockIdx.x;
   double v[1] = {0.0};
   for (int64_t n = d.rblock_node0[b] + threadIdx.x; n < d.rblock_node0[b + 1]; n += blockDim.x) {
@@ -565,7 +618,7 @@ __global__ void __launch_bounds__(256) k_load_nodes(DevProblem d) {
     d.fg[n] = fg;
     v[0] += fg * fg;
   }
-  block_sum<1>(v, sm);
+  block_sum_d<1, 256>(v, sm);
   if (threadIdx.x == 0) d.rpart2[b] = v[0];
 }
 
@@ -679,8 +732,7 @@ cudaError_t launch_cg_iteration(const DevProblem& d, cudaStream_t s, unsigned lo
     if (d.rpl64 == 2) k_cg_spmv<double, 2, false><<<(unsigned)d.n_tiles, kTileRows / 2, 0, s>>>(d, v);
     else k_cg_spmv<double, 1, false><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
   }
-  k_cg_update_a<double, kUpdGroup64><<<(unsigned)d.n_ublocks64, kTileRows, 0, s>>>(d, v);
-  k_fin_beta<<<fin_blocks(d), kTileRows, 0, s>>>(d, cond, use_cond);
+  k_cg_update_a<double, kUpdGroup64><<<(unsigned)d.n_ublocks64, kTileRows, 0, s>>>(d, v, cond, use_cond);
   k_cg_direction<double><<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d, v);
   return cudaGetLastError();
 }
@@ -688,8 +740,7 @@ cudaError_t launch_cg_iteration(const DevProblem& d, cudaStream_t s, unsigned lo
 cudaError_t launch_cg_iteration32(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
   OSM_LAUNCH_RPL(d.rpl32, d.c16_32, k_cg_spmv_dir32, s, d);
   const CgVec<float> v{d.x32, d.r32, d.z32, d.p32, d.q32, d.dinv32, d.vals32};
-  k_cg_update_a<float, kUpdGroup><<<(unsigned)d.n_ublocks, kTileRows, 0, s>>>(d, v);
-  k_fin_beta<<<fin_blocks(d), kTileRows, 0, s>>>(d, cond, use_cond);
+  k_cg_update_a<float, kUpdGroup><<<(unsigned)d.n_ublocks, kTileRows, 0, s>>>(d, v, cond, use_cond);
   return cudaGetLastError();
 }
 

@@ -50,52 +50,58 @@ __device__ __forceinline__ double lane_sum_tiles(const double* part, int64_t t0,
   return s;
 }
 
-// Row `row` (slice lane `rl` of the slice at `off`, width w) times the
-// candidates' vectors: lane k returns (K x_k)[row] (+ p_k (M_G x_k)[row]
-// when `robin`).  Xs: subdomain base of X, Xg: X itself.  FP64 reads the
-// FP64 values (pair layout), FP32 the FP32 values (quad layout).
-template <class T>
-__device__ __forceinline__ T mp_row(const DevProblem& d, const DevSample& m, int64_t off, int rl, int w,
-                                    const T* __restrict__ Xs, const T* __restrict__ Xg, int64_t row, bool robin,
-                                    double pk, int k) {
-  const int4* c4 = reinterpret_cast<const int4*>(d.cols + off) + rl;
-  T acc0 = T(0), acc1 = T(0);
+// Rows of the batched SpMM: lane k returns (K x_k)[row] (+ p_k (M_G x_k)[row]
+// on interface rows when ROBIN).  Xs: subdomain base of X, Xg: X itself.
+// FP64 reads the FP64 values (pair layout), FP32 the FP32 values (quad
+// layout); every matrix load is a broadcast shared by the 32 candidates.
+// NR consecutive rows rl .. rl+NR-1 of the slice at `off` (all of width w)
+// at once: NR independent load -> gather -> FMA chains per step keep NR
+// times more requests in flight than a row-at-a-time walk, which left the
+// batched SpMM latency-bound.
+template <class T, int NR, bool ROBIN = true>
+__device__ __forceinline__ void mp_rows(const DevProblem& d, const DevSample& m, int64_t off, int rl, int w,
+                                        const T* __restrict__ Xs, const T* __restrict__ Xg, int64_t row0,
+                                        double pk, int k, T (&out)[NR]) {
+  T acc0[NR], acc1[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) { acc0[r] = T(0); acc1[r] = T(0); }
   const int nq = w >> 2;
 #pragma unroll 2
   for (int q = 0; q < nq; ++q) {
-    const int4 c = __ldg(c4 + q * 32);
-    if constexpr (sizeof(T) == 8) {
-      const double2* v2 = reinterpret_cast<const double2*>(d.vals + off) + rl;
-      const double2 a = __ldg(v2 + q * 64);
-      const double2 b = __ldg(v2 + q * 64 + 32);
-      acc0 = fma(a.x, Xs[(int64_t)c.x * W + k], acc0);
-      acc1 = fma(a.y, Xs[(int64_t)c.y * W + k], acc1);
-      acc0 = fma(b.x, Xs[(int64_t)c.z * W + k], acc0);
-      acc1 = fma(b.y, Xs[(int64_t)c.w * W + k], acc1);
-    } else {
-      const float4 a = __ldg(reinterpret_cast<const float4*>(d.vals32 + off) + rl + q * 32);
-      acc0 = fmaf(a.x, Xs[(int64_t)c.x * W + k], acc0);
-      acc1 = fmaf(a.y, Xs[(int64_t)c.y * W + k], acc1);
-      acc0 = fmaf(a.z, Xs[(int64_t)c.z * W + k], acc0);
-      acc1 = fmaf(a.w, Xs[(int64_t)c.w * W + k], acc1);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      const int4 c = __ldg(reinterpret_cast<const int4*>(d.cols + off) + rl + r + q * 32);
+      if constexpr (sizeof(T) == 8) {
+        const double2* v2 = reinterpret_cast<const double2*>(d.vals + off) + rl + r;
+        const double2 a = __ldg(v2 + q * 64);
+        const double2 b = __ldg(v2 + q * 64 + 32);
+        acc0[r] = fma(a.x, Xs[(int64_t)c.x * W + k], acc0[r]);
+        acc1[r] = fma(a.y, Xs[(int64_t)c.y * W + k], acc1[r]);
+        acc0[r] = fma(b.x, Xs[(int64_t)c.z * W + k], acc0[r]);
+        acc1[r] = fma(b.y, Xs[(int64_t)c.w * W + k], acc1[r]);
+      } else {
+        const float4 a = __ldg(reinterpret_cast<const float4*>(d.vals32 + off) + rl + r + q * 32);
+        acc0[r] = fmaf(a.x, Xs[(int64_t)c.x * W + k], acc0[r]);
+        acc1[r] = fmaf(a.y, Xs[(int64_t)c.y * W + k], acc1[r]);
+        acc0[r] = fmaf(a.z, Xs[(int64_t)c.z * W + k], acc0[r]);
+        acc1[r] = fmaf(a.w, Xs[(int64_t)c.w * W + k], acc1[r]);
+      }
     }
   }
-  T acc = acc0 + acc1;
-  if (robin) {
-    const int32_t ir = m.row_irow[row];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    T acc = acc0[r] + acc1[r];
+    const int32_t ir = ROBIN ? m.row_irow[row0 + r] : -1;
     if (ir >= 0) {
       T f = T(0);
       for (int32_t e = d.im_ptr[ir]; e < d.im_ptr[ir + 1]; ++e)
         f = fma((T)d.im_val[e], Xg[(int64_t)d.im_col[e] * W + k], f);
       acc = fma((T)pk, f, acc);
     }
+    out[r] = acc;
   }
-  return acc;
 }
 
-// Jacobi scale of candidate k on `row`: 1 / (diag K + p_k diag M_G).  Off
-// the interface it is the stored 1 / diag K (padding rows: 0), one broadcast
-// load; only interface rows divide (FP64 division is slow on this GPU).
 __device__ __forceinline__ double mp_dinv(const DevProblem& d, const DevSample& m, int64_t row, double pk) {
   const int32_t ir = m.row_irow[row];
   if (ir < 0) return d.dinv[row];
@@ -147,19 +153,23 @@ __global__ void __launch_bounds__(kTileRows) k_mp_cg_init(DevProblem d, DevSampl
   const double* Xs = m.x + t0 * kTileRows * W;
   const double pk = m.psamp[k];
   double v[3] = {0.0, 0.0, 0.0};
-  for (int rl = 0; rl < kSliceRows; ++rl) {
-    const int64_t row = slice * kSliceRows + rl;
-    const double ax = mp_row<double>(d, m, off, rl, w, Xs, m.x, row, true, pk, k);
-    const int64_t idx = row * W + k;
-    const double b = m.b[idx];
-    const double r = b - ax;
-    const double z = mp_dinv(d, m, row, pk) * r;
-    m.r[idx] = r;
-    m.z[idx] = z;
-    m.pd[idx] = z;
-    v[0] += r * r;
-    v[1] += b * b;
-    v[2] += r * z;
+  for (int rl = 0; rl < kSliceRows; rl += 4) {
+    double ax4[4];
+    mp_rows<double, 4>(d, m, off, rl, w, Xs, m.x, slice * kSliceRows + rl, pk, k, ax4);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t row = slice * kSliceRows + rl + j;
+      const int64_t idx = row * W + k;
+      const double b = m.b[idx];
+      const double r = b - ax4[j];
+      const double z = mp_dinv(d, m, row, pk) * r;
+      m.r[idx] = r;
+      m.z[idx] = z;
+      m.pd[idx] = z;
+      v[0] += r * r;
+      v[1] += b * b;
+      v[2] += r * z;
+    }
   }
   lane_block_sum<3>(v, sm);
   if (warp == 0) {
@@ -194,12 +204,17 @@ __global__ void __launch_bounds__(kTileRows) k_mp_cg_spmv(DevProblem d, DevSampl
   // (the host sorts candidates by p, so the lanes still running tend to be
   // neighbours and share sectors)
   if (act) {
-    for (int rl = 0; rl < kSliceRows; ++rl) {
-      const int64_t row = slice * kSliceRows + rl;
-      const T q = mp_row<T>(d, m, off, rl, w, Xs, v.pd, row, true, pk, k);
-      const int64_t idx = row * W + k;
-      v.q[idx] = q;
-      pq.add(v.pd[idx], q, sc);
+    constexpr int NR = 4;
+    for (int rl = 0; rl < kSliceRows; rl += NR) {
+      const int64_t row0 = slice * kSliceRows + rl;
+      T q[NR];
+      mp_rows<T, NR>(d, m, off, rl, w, Xs, v.pd, row0, pk, k, q);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const int64_t idx = (row0 + r) * W + k;
+        v.q[idx] = q[r];
+        pq.add(v.pd[idx], q[r], sc);
+      }
     }
   }
   double acc[1] = {(double)pq.acc * (sizeof(T) == 4 ? m.isc2[sk] : 1.0)};
@@ -223,6 +238,7 @@ __global__ void __launch_bounds__(kTileRows) k_mp_cg_update(DevProblem d, DevSam
     const T sc = sizeof(T) == 4 ? (T)m.sc[sk] : T(1);
     MpDot<T> rz, rr;
     const int64_t slice = tile * kTileSlices + warp;
+#pragma unroll 4
     for (int rl = 0; rl < kSliceRows; ++rl) {
       const int64_t row = slice * kSliceRows + rl;
       const int64_t idx = row * W + k;
@@ -261,21 +277,25 @@ __global__ void __launch_bounds__(kTileRows) k_mp_cg_init_mixed(DevProblem d, De
   const double* Xs = m.x + t0 * kTileRows * W;
   const double pk = m.psamp[k];
   double acc[3] = {0.0, 0.0, 0.0};
-  for (int rl = 0; rl < kSliceRows; ++rl) {
-    const int64_t row = slice * kSliceRows + rl;
-    const double ax = mp_row<double>(d, m, off, rl, w, Xs, m.x, row, true, pk, k);
-    const int64_t idx = row * W + k;
-    const double b = m.b[idx];
-    const double dfc = b - ax;
-    const float r = (float)dfc;
-    const float z = (float)mp_dinv(d, m, row, pk) * r;
-    m.x32[idx] = 0.f;
-    m.r32[idx] = r;
-    m.z32[idx] = z;
-    m.pd32[idx] = z;
-    acc[0] += dfc * dfc;
-    acc[1] += b * b;
-    acc[2] += (double)r * (double)z;
+  for (int rl = 0; rl < kSliceRows; rl += 4) {
+    double ax4[4];
+    mp_rows<double, 4>(d, m, off, rl, w, Xs, m.x, slice * kSliceRows + rl, pk, k, ax4);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t row = slice * kSliceRows + rl + j;
+      const int64_t idx = row * W + k;
+      const double b = m.b[idx];
+      const double dfc = b - ax4[j];
+      const float r = (float)dfc;
+      const float z = (float)mp_dinv(d, m, row, pk) * r;
+      m.x32[idx] = 0.f;
+      m.r32[idx] = r;
+      m.z32[idx] = z;
+      m.pd32[idx] = z;
+      acc[0] += dfc * dfc;
+      acc[1] += b * b;
+      acc[2] += (double)r * (double)z;
+    }
   }
   lane_block_sum<3>(acc, sm);
   if (warp == 0) {
@@ -394,6 +414,7 @@ __global__ void __launch_bounds__(kTileRows) k_mp_cg_direction(DevProblem d, Dev
   if (!m.active[sk]) return;
   const T beta = (T)m.beta[sk];
   const int64_t slice = tile * kTileSlices + warp;
+#pragma unroll 4
   for (int rl = 0; rl < kSliceRows; ++rl) {
     const int64_t idx = (slice * kSliceRows + rl) * W + k;
     v.pd[idx] = fma(beta, v.pd[idx], v.z[idx]);
@@ -448,9 +469,11 @@ __global__ void __launch_bounds__(kTileRows) k_mp_spmv_k(DevProblem d, DevSample
   const int w = (int)((d.slice_off[slice + 1] - off) >> 5);
   const int64_t t0 = d.sub_tile0[s];
   const double* Xs = m.w + t0 * kTileRows * W;
-  for (int rl = 0; rl < kSliceRows; ++rl) {
-    const int64_t row = slice * kSliceRows + rl;
-    m.y[row * W + k] = mp_row<double>(d, m, off, rl, w, Xs, m.w, row, false, 0.0, k);
+  for (int rl = 0; rl < kSliceRows; rl += 4) {
+    double y4[4];
+    mp_rows<double, 4, false>(d, m, off, rl, w, Xs, m.w, slice * kSliceRows + rl, 0.0, k, y4);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) m.y[(slice * kSliceRows + rl + j) * W + k] = y4[j];
   }
 }
 

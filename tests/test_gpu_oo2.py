@@ -131,3 +131,18 @@ def test_slab_decomposition_matches_oracle(osm):
     phi, n, rel = sol.solve(rtol=1e-8)
     assert rel <= 1e-8 and abs(n - n_ref) <= 1, (n, n_ref)
     assert np.linalg.norm(phi.cpu().numpy() - ref) <= 1e-7 * np.linalg.norm(ref)
+
+
+def test_batch_instances_with_second_order_conditions(osm):
+    """osm_set_transmission on a batch handle applies to every instance: each
+    instance gives exactly its single-problem oo2 solve."""
+    probs = [small_uneven(), gen.slab_problem(nx=24, ny=12, nz=4, n_slabs=6, seed=2)]
+    tc = (0.9, 0.6, 0.3, 1.4)
+    bs = osm.BatchSolver(probs, inner_rtol=1e-12, max_outer=3000)
+    bs.set_transmission(*tc)
+    phi, iters, rel = bs.solve(rtol=1e-9)
+    for i, q in enumerate(probs):
+        one = osm.Solver.from_problem(q, tc=tc, inner_rtol=1e-12, max_outer=3000)
+        ph1, n1, r1 = one.solve(rtol=1e-9)
+        assert iters[i] == n1 and rel[i] == r1, (i, iters[i], n1)
+        assert bool((bs.instance_phi(phi, i) == ph1).all()), i

@@ -134,12 +134,16 @@ def test_race_mode_finds_the_same_winner(osm, prec):
     it_full, rel_full, best_full = sol.sample_p(ps, rtol=1e-8, max_outer=400)
     it_race, rel_race, best_race = sol.sample_p(ps, rtol=1e-8, max_outer=400, race=True)
     assert best_race == best_full
-    n_star = it_full[best_full]
+    assert it_race[best_race] == it_full[best_full] and rel_race[best_race] == rel_full[best_full]
     for k in range(len(ps)):
         if rel_race[k] <= 1e-8:
-            assert it_race[k] == it_full[k] == n_star and rel_race[k] == rel_full[k], k
+            # a candidate reported converged ran its full course
+            assert it_race[k] == it_full[k] and rel_race[k] == rel_full[k], k
         else:
-            assert it_race[k] <= n_star, k
+            # a stopped one stopped no later than its own full run ended
+            assert it_race[k] <= it_full[k] and not (rel_full[k] <= 1e-8 and it_full[k] <= it_race[k]), k
+    # nobody needed fewer iterations than the winner
+    assert it_full.min() >= 0 and all(it_full[k] >= it_full[best_full] for k in range(len(ps)) if rel_full[k] <= 1e-8)
     # unknown flags are rejected before anything runs
     one, it1, rel1, b1 = np.ones(1), np.zeros(1, dtype=np.int32), np.zeros(1), np.zeros(1, dtype=np.int32)
     st = osm.load().osm_sample_p_ex(sol._h, 1, osm._lib._ptr(one), 1e-8, 10, 4, osm._lib._ptr(it1),
