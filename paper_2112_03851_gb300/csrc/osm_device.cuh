@@ -89,50 +89,6 @@ __device__ __forceinline__ double warp_sum_parts(const double* part, int64_t t0,
   return warp_sum((v0 + v1) + (v2 + v3));
 }
 
-// One row of a SELL-32 slice: lane `lane` of the warp owning the slice at
-// `off` (width w, multiple of 4).  Matrix data is streamed (evict-first);
-// the gathered vector stays cached.
-__device__ __forceinline__ double sell_row(const int32_t* __restrict__ cols,
-                                           const double* __restrict__ vals, int64_t off, int w,
-                                           int lane, const double* __restrict__ x) {
-  const int4* c4 = reinterpret_cast<const int4*>(cols + off) + lane;
-  const double2* v2 = reinterpret_cast<const double2*>(vals + off) + lane;
-  double acc0 = 0.0, acc1 = 0.0;
-  const int nq = w >> 2;
-#pragma unroll 4
-  for (int q = 0; q < nq; ++q) {
-    const int4 c = __ldcs(c4 + q * 32);
-    const double2 a = __ldcs(v2 + q * 64);
-    const double2 b = __ldcs(v2 + q * 64 + 32);
-    acc0 = fma(a.x, __ldg(x + c.x), acc0);
-    acc1 = fma(a.y, __ldg(x + c.y), acc1);
-    acc0 = fma(b.x, __ldg(x + c.z), acc0);
-    acc1 = fma(b.y, __ldg(x + c.w), acc1);
-  }
-  return acc0 + acc1;
-}
-
-// FP32 values (mixed-precision inner solve): the value array uses the same
-// quad layout as the columns, so one float4 per lane per step; FP32 FMA
-// accumulation.
-__device__ __forceinline__ float sell_row(const int32_t* __restrict__ cols, const float* __restrict__ vals,
-                                          int64_t off, int w, int lane, const float* __restrict__ x) {
-  const int4* c4 = reinterpret_cast<const int4*>(cols + off) + lane;
-  const float4* v4 = reinterpret_cast<const float4*>(vals + off) + lane;
-  float acc0 = 0.f, acc1 = 0.f;
-  const int nq = w >> 2;
-#pragma unroll 4
-  for (int q = 0; q < nq; ++q) {
-    const int4 c = __ldcs(c4 + q * 32);
-    const float4 a = __ldcs(v4 + q * 32);
-    acc0 = fmaf(a.x, __ldg(x + c.x), acc0);
-    acc1 = fmaf(a.y, __ldg(x + c.y), acc1);
-    acc0 = fmaf(a.z, __ldg(x + c.z), acc0);
-    acc1 = fmaf(a.w, __ldg(x + c.w), acc1);
-  }
-  return acc0 + acc1;
-}
-
 // Rows of one 256-row tile handled by the calling thread when each warp works
 // RPL slices at once (blockDim = 256 / RPL): slice tile*8 + warp*RPL + k,
 // row slice*32 + lane.  The slices' loads are interleaved step by step, so a

@@ -8,11 +8,12 @@
 // lane).  Every kernel therefore runs all subdomains, of any size, in one
 // launch; converged subdomains' tiles return at once.
 //
-// Reductions are deterministic: each tile writes its partial sums, and a
-// small finaliser kernel (one warp per subdomain) adds a subdomain's partials
-// in a fixed order and updates that subdomain's CG scalars.  The finalisers
-// that steer a device-side loop take a last-block ticket across their few
-// blocks and call cudaGraphSetConditional from that single block.
+// Reductions are deterministic: each tile writes its partial sums, and one
+// warp adds a subdomain's partials in a fixed order (the start-of-solve
+// finaliser k_fin_init, and the last block of each subdomain in the CG
+// update).  Loop conditions are set with cudaGraphSetConditional by the last
+// arrival at a ticket (an atomic counter taken once per block or subdomain);
+// no kernel waits on another block.
 #include <cuda_runtime.h>
 
 #include "osm_device.cuh"
@@ -256,13 +257,13 @@ __global__ void __launch_bounds__(kTileRows) k_cg_direction(DevProblem d, CgVec<
   v.p[row] = fma((T)d.st.beta[s], v.p[row], v.z[row]);
 }
 
-// FP32 inner CG of the mixed form in three kernels per step.  With
-// t = A z, the direction update moves into the SpMV's epilogue:
+// FP32 inner CG of the mixed form in two kernels per step.  With t = A z,
+// the direction update moves into the SpMV's epilogue:
 //   p = z + beta p,   q = A p = t + beta q   (first step, beta = 0: p = z, q = t)
-// and alpha = rho / (p.q) is formed inside the update kernel (every block
-// of a subdomain adds the subdomain's p.q partials in the same fixed order),
-// so k_cg_direction and a separate alpha kernel drop out.  Same vector traffic as the
-// five-kernel step, two launches and one pass over the vectors fewer.
+// and alpha = rho / (p.q) and beta are formed inside the update kernel, so
+// k_cg_direction and the separate alpha and beta kernels of the textbook
+// step drop out: the same vector traffic, fewer launches and one pass over
+// the vectors fewer.
 template <int RPL, bool C16>
 __global__ void __launch_bounds__(kTileRows) k_cg_spmv_dir32(DevProblem d) {
   __shared__ double sm[1][kTileSlices];
