@@ -1029,15 +1029,25 @@ osm_status osm_stats(osm_handle h, osm_stats_t* o) {
   const DevCtl& c = *h->ctl_host;
   o->n_outer = c.n_outer;
   o->n_cg_steps = c.total_inner;
-  // per Schwarz iteration: RHS gather, CG start, its finaliser, exchange
-  // (if any face), average, SpMV, face correction (if any interface),
-  // residual, FP64 correction (mixed); per batched CG step: SpMV+dot, alpha,
-  // update, beta + loop control, direction
-  const int64_t per_outer = h->last_kind == 1
-                                ? 3 + (h->hp.n_fent ? 1 : 0) + 3
-                                : 3 + (h->hp.n_fent ? 1 : 0) + 3 + (h->hp.irow.empty() ? 0 : 1) +
-                                      (h->opts.prec == OSM_MIXED ? 1 : 0);
-  o->n_launches = per_outer * c.n_outer + 5 * (int64_t)c.total_inner;
+  // Kernel launches of the last call, counted from the launch sequence.
+  const int mixed = h->opts.prec == OSM_MIXED;
+  const int faces = h->hp.n_fent ? 1 : 0;
+  if (h->last_kind == 1) {
+    // batched p evaluation: per Schwarz iteration RHS gather, CG start, its
+    // finaliser, FP64 correction (mixed), exchange (if any face), average,
+    // K ubar, residual; per batched CG step SpMM, alpha, update, beta,
+    // direction; plus the start of the batch
+    const int64_t per_outer = 3 + mixed + faces + 3;
+    o->n_launches = 1 + per_outer * c.n_outer + 5 * (int64_t)c.total_inner;
+  } else {
+    // solve: per Schwarz iteration RHS gather, CG start, its finaliser, FP64
+    // correction (mixed), exchange (if any face), average, K ubar, face
+    // correction (if any interface), residual partials, residual finaliser;
+    // per CG step SpMV (+ direction epilogue in FP32) and update (+ the
+    // step's finish), plus the FP64 direction; plus the nodal load once
+    const int64_t per_outer = 3 + mixed + faces + 2 + (h->hp.irow.empty() ? 0 : 1) + 2;
+    o->n_launches = 1 + per_outer * c.n_outer + (mixed ? 2 : 3) * (int64_t)c.total_inner;
+  }
   o->relres = c.relres;
   o->status = c.status;
   o->reserved = 0;
