@@ -6,7 +6,8 @@
  * discretised by Q2 (27-node triquadratic) hexahedral finite elements
  * ("high order finite elements", Sec. 6), with the non-overlapping optimized
  * Schwarz method of Sec. 3 using the zeroth-order Robin transmission operator
- * A = p ("oo0"): every iteration solves all subdomain problems
+ * A = p ("oo0"; second-order and unsymmetric operators: osm_set_transmission):
+ * every iteration solves all subdomain problems
  *     (K_i + p_i M_Gi) u_i = f_i + sum_j lam_ij
  * by Jacobi-preconditioned CG (Sec. 6), all subdomains batched in the same
  * kernels, then exchanges the interface Robin data
@@ -65,9 +66,10 @@ typedef enum {
     OSM_FP64 = 0,   /* every step in FP64 */
     OSM_MIXED = 1,  /* per Schwarz iteration and subdomain: FP64 defect d = b - A u, one
                        FP32 CG solve of A e = d from e = 0 (FP32 matrix values, FP32
-                       vectors and accumulation, FP64 dot products) to
-                       ||r|| <= mixed_inner_rtol ||d||, then u += e in FP64; the Robin
-                       exchange and the stop test stay FP64 */
+                       vectors and accumulation; dot products of power-of-two-scaled
+                       factors summed in FP32 per warp and in FP64 across warps and
+                       tiles) to ||r|| <= mixed_inner_rtol ||d||, then u += e in FP64;
+                       the Robin exchange and the stop test stay FP64 */
     OSM_FP64_REFINE = 2 /* the OSM_MIXED algorithm in FP64: FP64 CG warm-started from u_i,
                            stopped at ||r|| <= mixed_inner_rtol times its initial residual
                            (the defect), subdomains whose defect meets inner_rtol skipped */
@@ -89,8 +91,10 @@ typedef struct {
     osm_precision prec;
     double inner_rtol;      /* FP64 subdomain CG stop ||b_i - A_i u_i|| <= inner_rtol ||b_i||
                                (Sec. 6 uses 1e-10) */
-    double mixed_inner_rtol;/* OSM_MIXED: FP32 CG stop on each correction, relative to the
-                               FP64 defect (default 1e-5) */
+    double mixed_inner_rtol;/* OSM_MIXED / OSM_FP64_REFINE: CG stop on each correction,
+                               relative to the FP64 defect, in (0, 1) (default 1e-5; the
+                               fastest on the 64^3 layered benchmark was 0.4-0.5: fewer CG
+                               steps for more Schwarz iterations) */
     int32_t max_outer;      /* Schwarz iteration cap (default 10000) */
     int32_t max_inner;      /* CG iteration cap per subdomain solve (default 20000) */
     int32_t use_graph;      /* 1 (default): the whole solve runs as one CUDA graph with
