@@ -352,6 +352,18 @@ def _measure(sol, prob, args, ws, local, barrier, use_graph_note, rtol=RTOL):
     }
 
 
+FP64_FMA_PEAK_GFLOPS = 1256.0   # measured FP64 FMA throughput (profiles/peaks.md)
+
+
+def _roofline_alu(sol, ms):
+    """The FP64 CG-step SpMV against the FP64 FMA pipe: two flops per nonzero
+    (one DFMA) in `ms` per launch."""
+    achieved = 2.0 * sol.info["nnz"] / (ms / 1e3) / 1e9
+    return {"bound": "alu", "achieved": round(achieved, 1), "peak": FP64_FMA_PEAK_GFLOPS, "unit": "GFLOP/s",
+            "frac": round(achieved / FP64_FMA_PEAK_GFLOPS, 4),
+            "peak_kind": "measured FP64 FMA probe (152 SMs x 2 DFMA/clk x 2.07 GHz = 1.26 TFLOP/s nominal)"}
+
+
 def _roofline(sol, prec, name):
     """Roofline of the CG-step SpMV kernel (prec 2: k_cg_spmv_dir32, 3:
     k_cg_spmv<double>), timed alone with every subdomain active."""
@@ -445,6 +457,7 @@ def run_ours(args):
         line["fp64"]["precision"] = f"FP64, subdomain PCG to {INNER_RTOL:g} of ||b_i|| every iteration (Sec. 6)"
         line["fp64"]["roofline"] = _roofline(sols["fp64"], 3, "k_cg_spmv<double> (batched SELL-32 FP64 SpMV of the "
                                                                "CG step, every subdomain active)")
+        line["fp64"]["roofline_alu"] = _roofline_alu(sols["fp64"], line["fp64"]["roofline"]["ms_per_launch"])
         line["mixed_speedup_vs_fp64"] = round(h["value"] / f["value"], 3)
     if "fp64_refine" in res:
         f = res["fp64_refine"]

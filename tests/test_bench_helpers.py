@@ -1,0 +1,42 @@
+"""Host-side helpers of bench.py (no GPU): rooflines and the per-kernel source
+hash that keys the committed ncu traffic."""
+import json
+from pathlib import Path
+
+import bench
+
+
+class _FakeSolver:
+    info = {"nnz": 129_600_000, "n_local": 2_197_000, "n_slices": 70_000, "col_bytes_fp64": 4, "col_bytes_fp32": 2}
+
+    def spmv_bytes(self, prec=0):
+        vb = 8 if prec in (0, 3) else 4
+        cb = self.info["col_bytes_fp64"] if prec in (0, 3) else self.info["col_bytes_fp32"]
+        extra = 12 * self.info["n_local"] if prec == 2 else 0
+        return self.info["nnz"] * (vb + cb) + self.info["n_slices"] * 8 + self.info["n_local"] * 2 * vb + extra
+
+    def profile_spmv(self, reps=20, prec=0):
+        return 0.25
+
+
+def test_alu_roofline_counts_one_fma_per_nonzero():
+    r = bench._roofline_alu(_FakeSolver(), 0.2592)
+    assert r["bound"] == "alu" and r["unit"] == "GFLOP/s"
+    assert abs(r["achieved"] - 1000.0) < 0.1 and abs(r["frac"] - 1000.0 / bench.FP64_FMA_PEAK_GFLOPS) < 1e-4
+
+
+def test_hbm_roofline_fields():
+    r = bench._roofline(_FakeSolver(), 3, "k")
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["ms_per_launch"] == 0.25
+    assert r["algorithmic_bytes"] == _FakeSolver().spmv_bytes(3)
+    assert abs(r["achieved"] - r["algorithmic_bytes"] / 0.25e-3 / 1e9) < 0.1
+
+
+def test_traffic_key_matches_the_committed_capture():
+    """The committed ncu traffic of the FP32 CG-step SpMV is keyed to its
+    current source: editing that kernel (or a helper it calls) drops it."""
+    d = json.loads((Path(bench.ROOT) / "profiles" / "cg_spmv_layered48_traffic.json").read_text())
+    e = d["k_cg_spmv_dir32"]
+    assert e["kernel_hash"] == bench._kernel_hash("k_cg_spmv_dir32")
+    assert bench._traffic_per_launch(1000, "k_cg_spmv_dir32", e["col_bytes"]) == round(e["dram_bytes_per_row"] * 1000)
+    assert bench._traffic_per_launch(1000, "k_cg_spmv_dir32", 4 if e["col_bytes"] == 2 else 2) is None
