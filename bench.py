@@ -57,14 +57,11 @@ def _tc_for(prob, name):
     spacing.  Others: None (zeroth-order Robin, P_FOR)."""
     if not _is_slab(name):
         return None
-    import math
-
     from paper_2112_03851_gb300 import search
     ly, lz = prob.yc[-1] - prob.yc[0], prob.zc[-1] - prob.zc[0]
     h = min(float((prob.yc[1:] - prob.yc[:-1]).min()), float((prob.zc[1:] - prob.zc[:-1]).min()))
-    kmin, kmax = math.pi * math.hypot(1.0 / ly, 1.0 / lz), math.pi / (0.5 * h)
-    c, rho, _ = search.optimise_fourier("oo2_unsym", kmin, kmax, seed=0, max_iter=2000)
-    return tuple(float(v) for v in c), float(rho), (kmin, kmax)
+    tc, rho, band = search.transmission_for_faces(ly, lz, h, "oo2_unsym", seed=0, max_iter=2000)
+    return tc, float(rho), band
 
 
 def _workload_desc(prob, p, name=WORKLOAD, tc=None):

@@ -155,6 +155,36 @@ def optimise_fourier(kind="oo0_sym", kmin=0.0174, kmax=1.915, seed=0, max_iter=7
     return np.exp(res.x), res.f, res
 
 
+def interface_band(extent_a, extent_b, h):
+    """Frequency band of an interface face with tangential extents a x b and
+    smallest tangential element size h: from the lowest Dirichlet mode,
+    pi sqrt(1/a^2 + 1/b^2), to pi over the Q2 node spacing h/2."""
+    return math.pi * math.hypot(1.0 / extent_a, 1.0 / extent_b), math.pi / (0.5 * h)
+
+
+def coefficients(kind, x):
+    """(p_lo, q_lo, p_hi, q_hi) for osm_set_transmission from optimised
+    parameters: the lower side of a face plays Omega^(1) of Sec. 3."""
+    x = [float(v) for v in x]
+    if kind == "oo0_sym":
+        return (x[0], 0.0, x[0], 0.0)
+    if kind == "oo0_unsym":
+        return (x[0], 0.0, x[1], 0.0)
+    if kind == "oo2_sym":
+        return (x[0], x[1], x[0], x[1])
+    if kind == "oo2_unsym":
+        return (x[0], x[1], x[2], x[3])
+    raise ValueError(kind)
+
+
+def transmission_for_faces(extent_a, extent_b, h, kind="oo2_unsym", seed=0, max_iter=2000):
+    """Sec. 4's procedure for a given mesh: CMA-ES on the Fourier rate over
+    the faces' band.  Returns (p_lo, q_lo, p_hi, q_hi), rho_max, band."""
+    kmin, kmax = interface_band(extent_a, extent_b, h)
+    c, rho, _ = optimise_fourier(kind, kmin, kmax, seed=seed, max_iter=max_iter)
+    return coefficients(kind, c), rho, (kmin, kmax)
+
+
 # ------------------------------------------------- Schwarz iteration cost --
 
 def schwarz_iterations_cost(solver, rtol=1e-8, max_outer=400, race=True):

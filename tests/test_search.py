@@ -65,3 +65,25 @@ def test_cma_es_matches_or_beats_table1(kind):
 def test_cma_es_on_a_quadratic():
     res = search.cma_es(lambda X: np.sum((X - 3.0) ** 2, axis=1), np.zeros(3), 1.0, popsize=12, seed=2)
     assert np.allclose(res.x, 3.0, atol=1e-5) and res.stop in ("tol", "sigma")
+
+
+def test_optimised_conditions_rank_like_table1_on_a_slab_chain():
+    """Sec. 3-4 on the oracle: on an x-slab chain of the paper's box, the
+    conditions CMA-ES optimises on the Fourier rate of the faces' band need
+    fewer Schwarz iterations in the order of Table 1's rho_max (oo0 sym >
+    oo0 unsym > oo2 sym >= oo2 unsym)."""
+    import gen
+    import oracle
+    prob = gen.slab_problem(nx=24, ny=12, nz=4, n_slabs=6, seed=2)
+    ly, lz = prob.yc[-1] - prob.yc[0], prob.zc[-1] - prob.zc[0]
+    h = min(np.diff(prob.yc).min(), np.diff(prob.zc).min())
+    its, rhos = [], []
+    for kind in ("oo0_sym", "oo0_unsym", "oo2_sym", "oo2_unsym"):
+        tc, rho, _ = search.transmission_for_faces(ly, lz, h, kind)
+        S = oracle.Schwarz.from_problem(prob, tc=tc)
+        _, n, rel, _ = S.solve(inner_rtol=1e-12, rtol=1e-8, max_outer=3000)
+        assert rel <= 1e-8
+        its.append(n)
+        rhos.append(rho)
+    assert rhos[0] > rhos[1] > rhos[2] > rhos[3]
+    assert its[0] > its[1] > its[2] >= its[3], its
