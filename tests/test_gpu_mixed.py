@@ -149,3 +149,16 @@ def test_32bit_columns_for_large_subdomains(osm):
     phi, n, rel = sol.solve(rtol=1e-9)
     G = oracle.GlobalSystem(prob.xc, prob.yc, prob.zc, prob.drho)
     assert G.residual(phi.cpu().numpy()) <= 1.001e-9
+
+
+def test_regional_full_size_mixed_residual(osm):
+    """The regional workload at full size (128 x 128 x 48 graded Q2, 6.18M
+    unknowns, 192 uneven subdomains from jittered cuts) in the launch
+    configuration the benchmark times: mixed precision, inner tolerance 0.4,
+    to 1e-8.  The oracle's own assembled K certifies ||f - K phi|| <= rtol ||f||."""
+    prob = gen.workload("regional")
+    sol = osm.Solver.from_problem(prob, p=1.0, prec="mixed", mixed_inner_rtol=0.4, max_outer=5000)
+    phi, n, rel = sol.solve(rtol=1e-8)
+    assert rel <= 1e-8
+    G = oracle.GlobalSystem(prob.xc, prob.yc, prob.zc, prob.drho)
+    assert G.residual(phi.cpu().numpy()) <= 1.001e-8
