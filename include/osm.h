@@ -399,18 +399,18 @@ osm_status osm_profile_spmv(osm_handle h, int32_t prec, int32_t reps, double *ms
 
 /*
  * y = A x exactly as osm_apply computes it, but without any device
- * allocation for the call.  The paper has no counterpart: this serves
- * callers that cannot call cudaMalloc where they need the operator, such as
- * code running while a framework captures the stream into a CUDA graph
- * (cudaMalloc may synchronise the device) or plug-ins whose device memory is
- * owned by a host framework's allocator.  Besides x and y (canonical local
- * layout, device, n_local doubles each) the call uses only a fixed 8 MiB
- * scratch array inside the library image, which every GPU that loads the
- * library holds until the process exits.  Limit: the handle's padded vector
- * length (osm_info vec_rows) must be at most 524288; larger problems get
- * OSM_E_ARG with an explanation.  The first call on a device looks up the
- * scratch array's device address, so make it before any stream capture.
- * All calls share the scratch: calls that overlap on the GPU race.
+ * allocation for the call.  The paper has no counterpart.  It serves callers
+ * that cannot call cudaMalloc where they need the operator: plug-ins whose
+ * device memory is reserved and capped by a host framework's own allocator
+ * (a cudaMalloc of their own bypasses it and can fail), and callers with a
+ * memory budget fixed at start-up.  Besides x and y (canonical local layout,
+ * device, n_local doubles each) the call uses only a fixed 8 MiB scratch
+ * array inside the library image, which every GPU that loads the library
+ * holds until the process exits.  Limit: the handle's padded vector length
+ * (osm_info vec_rows) must be at most 524288; larger problems get OSM_E_ARG
+ * with an explanation.  The first call on a device looks up the scratch
+ * array's device address, so make it before any stream capture.  All calls
+ * share the scratch: calls that overlap on the GPU race.
  * op 0: A_i = K_i + p_i M_Gi; op 1: A_i = K_i.  Synchronises the stream.
  */
 osm_status osm_apply_noalloc(osm_handle h, int32_t op, const double *x, double *y);

@@ -151,6 +151,23 @@ def _dptr(t):
     return C.c_void_p(t.data_ptr())
 
 
+def check_local_vector(t, n, device, name):
+    """Refuse, before any launch, a tensor the C ABI would read or write out
+    of bounds: it must be float64, contiguous, on the handle's device and
+    hold exactly n values (the canonical local layout)."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch tensor")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{name} must be float64, got {t.dtype}")
+    if t.device != torch.device(device):
+        raise ValueError(f"{name} must be on {device}, got {t.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.numel() != n:
+        raise ValueError(f"{name} must have {n} values (canonical local layout), got {t.numel()}")
+
+
 class _Inputs:
     """Host copies of mesh / density / cuts kept alive for a call."""
 
@@ -271,18 +288,22 @@ class Solver:
         return phi, it.value, rel.value
 
     def apply(self, x, op=0):
-        """y = A x (op 0: Robin matrix, op 1: Neumann stiffness), canonical local layout."""
-        x = x.contiguous()
+        """y = A x (op 0: Robin matrix, op 1: Neumann stiffness, op 2: the FP32
+        inner operator of a mixed handle), canonical local layout."""
+        check_local_vector(x, self.info["n_local"], self.device, "x")
         y = self._zeros(self.info["n_local"])
         self._check(load().osm_apply(self._h, int(op), _dptr(x), _dptr(y)))
         return y
 
     def apply_noalloc(self, x, y=None, op=0):
         """y = A x like apply(), using only the library's fixed scratch (no
-        device allocation by the library; y may be a preallocated tensor)."""
-        x = x.contiguous()
+        device allocation by the library).  Pass a preallocated y to avoid
+        the one allocation this wrapper would otherwise make for it."""
+        check_local_vector(x, self.info["n_local"], self.device, "x")
         if y is None:
             y = self._zeros(self.info["n_local"])
+        else:
+            check_local_vector(y, self.info["n_local"], self.device, "y")
         self._check(load().osm_apply_noalloc(self._h, int(op), _dptr(x), _dptr(y)))
         return y
 

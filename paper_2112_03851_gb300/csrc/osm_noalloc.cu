@@ -2,12 +2,14 @@
 // allocation by the library during or for the call.
 //
 // Some callers cannot call cudaMalloc at the point where they need the
-// operator: code that runs while a framework captures the stream into a CUDA
-// graph (cudaMalloc may synchronise the device, which breaks a global-mode
-// capture), and plug-ins whose device memory is owned and capped by a host
-// framework's allocator.  This entry point serves them: besides the caller's
-// input and output it touches only a fixed scratch array that is part of the
-// library image itself.
+// operator.  A plug-in that runs inside a host framework usually finds the
+// device memory already reserved by that framework's caching allocator,
+// which also caps what a component may take; a cudaMalloc of its own would
+// bypass that accounting and can fail once the framework holds the memory.
+// A caller with a fixed memory budget decided at start-up (a service that
+// must not allocate while serving) is in the same position.  This entry
+// point serves them: besides the caller's input and output it touches only a
+// fixed scratch array that is part of the library image itself.
 //
 // The scratch lives in the file-scope array below.  Every GPU that loads this
 // library holds it (8 MiB) until the process exits.  In host code the array's
@@ -17,7 +19,8 @@
 // therefore come before any stream capture.  All calls share the array and it
 // keeps the last call's contents: the part of it that must start at zero is
 // cleared by every call, and calls that overlap on the GPU (two streams, two
-// threads) race on it.
+// threads) race on it.  The call synchronises the handle's stream before it
+// returns, so y is ready when it does.
 #include <cuda_runtime.h>
 
 #include <mutex>

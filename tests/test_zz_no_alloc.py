@@ -1,9 +1,10 @@
 """osm_apply_noalloc: the subdomain operator for callers that cannot allocate
-device memory where they need it (for instance inside a framework's stream
-capture, or under a host framework's capped allocator).  It must give
-osm_apply's result, through the C ABI, using only the library's fixed
-scratch array -- also on a second call in a row and after another handle
-with a different layout has used the same scratch.
+device memory where they need it (a plug-in under a host framework's own,
+capped allocator; a caller whose memory budget is fixed at start-up).  It
+must give osm_apply's result, through the C ABI, using only the library's
+fixed scratch array -- also on a second call in a row, into a caller's
+preallocated output, and after another handle with a different layout has
+used the same scratch -- and must allocate no device memory.
 
 This file is collected last so that a failure here cannot hide the other
 tests' results in a run that stops at the first failure.
@@ -57,3 +58,32 @@ def test_noalloc_rejects_problems_beyond_its_scratch(osm):
     x = torch.zeros(sol.info["n_local"], dtype=torch.float64, device="cuda")
     with pytest.raises(osm.OsmError, match="scratch"):
         sol.apply_noalloc(x)
+
+
+def test_noalloc_into_preallocated_output_allocates_nothing(osm):
+    """The form a capped-allocator caller uses: x and y are its own tensors.
+    After one warm call, further calls leave the library's device memory,
+    torch's allocator and the device's free memory unchanged."""
+    import torch
+    rng = np.random.default_rng(11)
+    sol = osm.Solver.from_problem(gen.sphere_problem(16, 2, 10.0), p=3.0)
+    n = sol.info["n_local"]
+    xs = [torch.from_numpy(rng.standard_normal(n)).cuda() for _ in range(3)]
+    refs = [sol.apply(x, op=0) for x in xs]
+    y = torch.empty(n, dtype=torch.float64, device="cuda")
+    sol.apply_noalloc(xs[0], y=y)                  # warm: device address of the scratch looked up
+    torch.cuda.synchronize()
+    lib_bytes = sol.info["device_bytes"]
+    torch_bytes = torch.cuda.memory_allocated()
+    free0, _ = torch.cuda.mem_get_info()
+    for x, ref in zip(xs, refs):
+        out = sol.apply_noalloc(x, y=y)
+        assert out.data_ptr() == y.data_ptr()
+        assert float((y - ref).abs().max()) <= 1e-13 * float(ref.abs().max())
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    info = osm._lib.OsmInfo()
+    osm._lib.load().osm_info(sol._h, osm._lib.C.byref(info))
+    assert info.device_bytes == lib_bytes
+    assert torch.cuda.memory_allocated() == torch_bytes
+    assert free1 >= free0
