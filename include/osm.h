@@ -110,7 +110,17 @@ typedef struct {
                                instead of 12 bytes per nonzero, FP32: 6 instead of 8); the
                                autotuner picks the width per precision (with autotune != 1
                                the 16-bit ones are used); 0: always 32 bits */
-    int32_t reserved[2];
+    int32_t fp32_operator;  /* OSM_MIXED: the operator of the FP32 inner CG.  0 (default):
+                               chosen by the autotuner (timing both CG-step kernels);
+                               1: the FP32 SELL matrix; 2: the tensor-product form
+                               K_i = Kx (x) My (x) Mz + Mx (x) Ky (x) Mz + Mx (x) My (x) Kz of
+                               the assembled 1-D Q2 operators, applied matrix-free by sum
+                               factorisation, with the Robin term p M_G folded into the
+                               1-D stiffness at interface ends.  The tensor form holds for
+                               zeroth-order transmission (q = 0) only: with q != 0 the
+                               handle uses the SELL matrix.  Boxes wider than 128 nodes
+                               along x also keep the SELL matrix. */
+    int32_t reserved;
 } osm_opts;
 
 typedef struct {
@@ -134,6 +144,13 @@ typedef struct {
     double spmv_ms16_fp32[2];
     int32_t col_bytes_fp64;      /* bytes per column index read by the FP64 SpMVs (2 or 4) */
     int32_t col_bytes_fp32;      /* ... by the FP32 SpMVs (0 without OSM_MIXED) */
+    int32_t fp32_operator;       /* operator of the FP32 inner CG in use: 1 SELL, 2 tensor
+                                    product (0 without OSM_MIXED) */
+    int32_t fp32_operator_tuned; /* the autotuner's (or opts.fp32_operator's) choice, used
+                                    whenever the transmission condition allows it */
+    double tensor_ms_fp32;       /* autotuner timing of the tensor-product CG-step kernel
+                                    (ms, 0 if not run) */
+    int64_t box_rows;            /* rows of the box layout of the tensor form (0 if none) */
 } osm_info_t;
 
 typedef struct {

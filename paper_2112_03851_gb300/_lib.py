@@ -41,7 +41,7 @@ class OsmOpts(C.Structure):
     _fields_ = [("prec", C.c_int32), ("inner_rtol", C.c_double), ("mixed_inner_rtol", C.c_double),
                 ("max_outer", C.c_int32), ("max_inner", C.c_int32), ("use_graph", C.c_int32),
                 ("max_seconds", C.c_int32), ("autotune", C.c_int32), ("index16", C.c_int32),
-                ("reserved", C.c_int32 * 2)]
+                ("fp32_operator", C.c_int32), ("reserved", C.c_int32)]
 
 
 class OsmInfo(C.Structure):
@@ -53,7 +53,9 @@ class OsmInfo(C.Structure):
                 ("spmv_variant_fp64", C.c_int32), ("spmv_variant_fp32", C.c_int32),
                 ("spmv_ms_fp64", C.c_double * 2), ("spmv_ms_fp32", C.c_double * 2),
                 ("spmv_ms16_fp64", C.c_double * 2), ("spmv_ms16_fp32", C.c_double * 2),
-                ("col_bytes_fp64", C.c_int32), ("col_bytes_fp32", C.c_int32)]
+                ("col_bytes_fp64", C.c_int32), ("col_bytes_fp32", C.c_int32),
+                ("fp32_operator", C.c_int32), ("fp32_operator_tuned", C.c_int32),
+                ("tensor_ms_fp32", C.c_double), ("box_rows", C.c_int64)]
 
 
 def _info_dict(info):
@@ -399,8 +401,14 @@ class Solver:
         nonzero the value (8 B FP64 or 4 B FP32) and its column index (4 B, or
         2 B on a handle with 16-bit indices), 8 B per slice offset, the input
         vector read once and the output written once; the FP32 CG-step kernel
-        (2) also reads p and q and writes p (12 B per row)."""
+        (2) also reads p and q and writes p (12 B per row).  The tensor-product
+        FP32 operator (info fp32_operator == 2) reads no matrix: per box row
+        the input read once and the output written once (+ 12 B for the CG
+        step's p, q epilogue); its 1-D bands (40 B per node of a box edge)
+        are under 0.1% of that and not counted."""
         i = self.info
+        if prec in (1, 2) and i.get("fp32_operator") == 2:
+            return i["box_rows"] * (8 + (12 if prec == 2 else 0))
         vb = 8 if prec in (0, 3) else 4
         cb = i["col_bytes_fp64"] if prec in (0, 3) else (i["col_bytes_fp32"] or 4)
         extra = 12 * i["n_local"] if prec == 2 else 0

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libosm.so")
-SOURCES = ["osm_api.cu", "osm_kernels.cu", "osm_setup_host.cpp", "osm_noalloc.cu", "osm_sample.cu", "osm_adjoint.cu"]
+SOURCES = ["osm_api.cu", "osm_kernels.cu", "osm_setup_host.cpp", "osm_noalloc.cu", "osm_sample.cu", "osm_adjoint.cu", "osm_tensor.cu"]
 HEADERS = ["osm_internal.h", "osm_device.cuh", os.path.join("..", "..", "include", "osm.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -52,6 +52,10 @@ struct osm_ctx {
   cudaGraphExec_t mp_exec = nullptr;
   int last_kind = 0;            // 0: single solve / iterate, 1: batched p evaluation
   double tune_ms[2][4] = {};  // [fp64, fp32][2 c16 + rpl - 1]
+  // tensor-product FP32 operator (mixed handles whose boxes fit the kernel)
+  bool have_box = false;
+  int fp32_tuned = 1;           // 1: SELL, 2: tensor product (autotuner or opts.fp32_operator)
+  double tune_tensor_ms = 0.0;
   // adjoint gradient (allocated on first use)
   bool adj_ready = false;
   DevAdjoint adj{};
@@ -152,7 +156,14 @@ osm_status upload_problem(osm_ctx* h) {
   OSM_CUDA(h, dalloc(h, &st.ucnt, ns));
   OSM_CUDA(h, dalloc(h, &st.sc, ns));
   OSM_CUDA(h, dalloc(h, &st.isc2, ns));
-  for (double** v : {&d.part0, &d.part1, &d.part2}) OSM_CUDA(h, dalloc(h, v, hp.n_tiles));
+  // the tensor form of the FP32 operator (mixed handles): box layout tables
+  if (h->opts.prec == OSM_MIXED && h->opts.fp32_operator != 1 && !hp.row_boxidx.empty()) {
+    build_box_layout(hp);
+    h->have_box = hp.box_max_nx <= kTensorMaxNx && hp.box_rows < ((int64_t)1 << 31);
+  }
+  const size_t nparts = h->have_box ? (size_t)std::max({hp.n_tiles, hp.box_tiles, hp.box_ctas}) : (size_t)hp.n_tiles;
+  for (double** v : {&d.part0, &d.part1, &d.part2}) OSM_CUDA(h, dalloc(h, v, nparts));
+  d.sub_part0 = sub_tile0;
   // interface rows
   d.n_irow = (int32_t)hp.irow.size();
   int32_t *irow, *irow_sub, *ilam_ptr, *ilam, *im_ptr, *im_col;
@@ -231,9 +242,41 @@ osm_status upload_problem(osm_ctx* h) {
     int64_t* ip32;
     OSM_CUDA(h, upload(h, &ip32, hp.im_pos32));
     d.im_pos32 = ip32;
-    for (float** v : {&d.x32, &d.r32, &d.z32, &d.p32, &d.q32}) OSM_CUDA(h, dalloc(h, v, nv));
+    const size_t nv32 = h->have_box ? std::max<size_t>(nv, (size_t)hp.box_rows) : nv;
+    for (float** v : {&d.x32, &d.r32, &d.z32, &d.p32, &d.q32}) OSM_CUDA(h, dalloc(h, v, nv32));
     std::vector<float> di32(hp.dinv0.begin(), hp.dinv0.end());
     OSM_CUDA(h, upload(h, &d.dinv32, di32));
+    if (h->have_box) {
+      int32_t *row_box, *box_dims, *box_band0, *box_tile_sub, *cta_sub;
+      int64_t *box_voff, *box_sub_tile0, *box_ub_tile0, *sub_cta0;
+      OSM_CUDA(h, upload(h, &row_box, hp.row_box));
+      OSM_CUDA(h, upload(h, &box_voff, hp.box_voff));
+      OSM_CUDA(h, upload(h, &box_dims, hp.box_dims));
+      std::vector<int32_t> band0(ns);
+      for (size_t s = 0; s < ns; ++s) band0[s] = hp.sub[s].band0;
+      OSM_CUDA(h, upload(h, &box_band0, band0));
+      OSM_CUDA(h, upload(h, &box_tile_sub, hp.box_tile_sub));
+      OSM_CUDA(h, upload(h, &box_sub_tile0, hp.box_sub_tile0));
+      OSM_CUDA(h, upload(h, &box_ub_tile0, hp.box_ub_tile0));
+      OSM_CUDA(h, upload(h, &cta_sub, hp.box_cta_sub));
+      OSM_CUDA(h, upload(h, &sub_cta0, hp.box_sub_cta0));
+      d.row_box = row_box; d.box_voff = box_voff; d.box_dims = box_dims; d.box_band0 = box_band0;
+      d.box_tile_sub = box_tile_sub; d.box_sub_tile0 = box_sub_tile0; d.box_ub_tile0 = box_ub_tile0;
+      d.cta_sub = cta_sub; d.sub_cta0 = sub_cta0;
+      d.box_n_tiles = hp.box_tiles;
+      d.box_n_ublocks = (int64_t)hp.box_ub_tile0.size();
+      d.n_cta32 = hp.box_ctas;
+      double *bk, *bm;
+      OSM_CUDA(h, upload(h, &bk, hp.band_k));
+      OSM_CUDA(h, upload(h, &bm, hp.band_m));
+      d.band_k = bk; d.band_m = bm;
+      OSM_CUDA(h, dalloc(h, &d.cK32, hp.band_k.size()));
+      OSM_CUDA(h, dalloc(h, &d.cM32, hp.band_m.size()));
+      std::vector<float> dib(hp.box_rows, 0.f);
+      for (int64_t r = 0; r < hp.vec_rows; ++r)
+        if (hp.row_box[r] >= 0) dib[hp.row_box[r]] = (float)hp.dinv0[r];
+      OSM_CUDA(h, upload(h, &d.dinv32b, dib));
+    }
   }
   return OSM_OK;
 }
@@ -242,12 +285,46 @@ osm_status upload_problem(osm_ctx* h) {
 // q_hi per subdomain; psub_host: the Robin parameter of the zeroth-order
 // symmetric form, used by the batched p evaluation and the p-derivative) and
 // forms the local matrices and Jacobi diagonals.
+osm_status select_fp32_operator(osm_ctx* h);
+
 osm_status apply_robin(osm_ctx* h) {
   OSM_CUDA(h, cudaMemcpyAsync(h->d.psub, h->psub_host.data(), sizeof(double) * h->hp.nsub,
                               cudaMemcpyHostToDevice, h->stream));
   OSM_CUDA(h, cudaMemcpyAsync(h->d.tc, h->tc_host.data(), sizeof(double) * 4 * h->hp.nsub,
                               cudaMemcpyHostToDevice, h->stream));
   OSM_CUDA(h, launch_set_robin(h->d, h->stream));
+  if (h->have_box) OSM_CUDA(h, launch_tensor_coef(h->d, h->stream));
+  return select_fp32_operator(h);
+}
+
+void drop_graphs(osm_ctx* h) {
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  if (h->graph) cudaGraphDestroy(h->graph);
+  if (h->mp_exec) cudaGraphExecDestroy(h->mp_exec);
+  if (h->mp_graph) cudaGraphDestroy(h->mp_graph);
+  if (h->ls_exec) cudaGraphExecDestroy(h->ls_exec);
+  if (h->ls_graph) cudaGraphDestroy(h->ls_graph);
+  h->exec = nullptr; h->graph = nullptr;
+  h->mp_exec = nullptr; h->mp_graph = nullptr;
+  h->ls_exec = nullptr; h->ls_graph = nullptr;
+}
+
+// The FP32 inner solve runs the tensor-product operator when it was chosen
+// and every transmission coefficient q is zero (the tensor form folds p M_G
+// only); otherwise the SELL matrix.  A change of layout rebuilds the solve
+// graphs (they hold the kernel arguments) and clears the FP32 vectors, whose
+// rows mean different nodes in the two layouts.
+osm_status select_fp32_operator(osm_ctx* h) {
+  bool q_zero = true;
+  for (size_t s = 0; s < h->tc_host.size() / 4; ++s)
+    if (h->tc_host[4 * s + 1] != 0.0 || h->tc_host[4 * s + 3] != 0.0) q_zero = false;
+  const int want = (h->have_box && h->fp32_tuned == 2 && q_zero) ? 1 : 0;
+  if (want == h->d.t32) return OSM_OK;
+  h->d.t32 = want;
+  drop_graphs(h);
+  const size_t n32 = std::max<size_t>((size_t)h->hp.vec_rows, (size_t)h->hp.box_rows);
+  for (float* v : {h->d.x32, h->d.r32, h->d.z32, h->d.p32, h->d.q32})
+    OSM_CUDA(h, cudaMemsetAsync(v, 0, sizeof(float) * n32, h->stream));
   return OSM_OK;
 }
 
@@ -419,25 +496,45 @@ osm_status build_mp_graph(osm_ctx* h) {
   return OSM_OK;
 }
 
-// Autotuner: time each SpMV variant (1 or 2 SELL slices per warp) on this
-// handle's matrices and keep the faster one per precision.
-// Times the plain SpMV of each precision in every variant -- one or two SELL
-// slices per warp, 32- or (if stored) 16-bit columns -- and keeps the fastest.
+// Autotuner: times the CG step's SpMV-bearing kernel of each precision, in
+// every variant, on this handle's own matrices and keeps the fastest:
+//  FP64: k_cg_spmv<double> with one or two SELL slices per warp and 32- or
+//        (if stored) 16-bit column indices;
+//  FP32 (mixed): k_cg_spmv_dir32 in the same four variants and, when the
+//        handle's boxes fit it, the tensor-product kernel.
 // 16-bit columns cut the bytes, but unpacking them costs integer issue slots,
-// which the FP64 SpMV (near the FP64 FMA limit) may not have to spare.
+// which the FP64 SpMV (near the FP64 FMA limit) may not have to spare.  The
+// kernels run in the profiling state (every subdomain active) on the
+// handle's current vectors (zero at setup); the variant chosen for the CG
+// step also serves the CG start and the stop test of that precision.
 osm_status autotune_spmv(osm_ctx* h) {
   const int fixed = h->opts.autotune == 2 ? 2 : 1;
   const int have16 = h->d.cols16 != nullptr;
+  const bool mixed = h->opts.prec == OSM_MIXED;
   h->d.rpl64 = fixed;
-  h->d.rpl32 = h->opts.prec == OSM_MIXED ? fixed : 0;
+  h->d.rpl32 = mixed ? fixed : 0;
   h->d.c16_64 = have16;
-  h->d.c16_32 = have16 && h->opts.prec == OSM_MIXED;
-  if (h->opts.autotune != 1) return OSM_OK;
+  h->d.c16_32 = have16 && mixed;
+  h->fp32_tuned = (mixed && h->have_box && h->opts.fp32_operator == 2) ? 2 : 1;
+  if (h->opts.autotune != 1) return select_fp32_operator(h);
+  h->d.t32 = 0;   // the SELL variants first (vectors are zero: no layout to clear)
+  OSM_CUDA(h, launch_profile_state(h->d, h->stream));
   cudaEvent_t e0, e1;
   OSM_CUDA(h, cudaEventCreate(&e0));
   OSM_CUDA(h, cudaEventCreate(&e1));
   cudaError_t e = cudaSuccess;
-  for (int prec = 0; prec < (h->opts.prec == OSM_MIXED ? 2 : 1) && e == cudaSuccess; ++prec) {
+  auto time_kernel = [&](int fp32, double* out) {
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = launch_cg_spmv_alone(h->d, fp32, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = launch_cg_spmv_alone(h->d, fp32, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    *out = ms / 5.0;
+  };
+  double best_sell32 = 1e300;
+  for (int prec = 0; prec < (mixed ? 2 : 1) && e == cudaSuccess; ++prec) {
     int best_rpl = 1, best_c16 = 0;
     double best_ms = 1e300;
     int32_t& rpl_ref = prec == 0 ? h->d.rpl64 : h->d.rpl32;
@@ -446,31 +543,34 @@ osm_status autotune_spmv(osm_ctx* h) {
       for (int rpl = 1; rpl <= 2 && e == cudaSuccess; ++rpl) {
         rpl_ref = rpl;
         c16_ref = c16;
-        auto launch = [&]() {
-          return prec == 0 ? launch_spmv_plain(h->d, h->d.w, h->d.y, h->stream)
-                           : launch_spmv_plain32(h->d, h->d.z32, h->d.q32, h->stream);
-        };
-        for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = launch();
-        if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
-        for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = launch();
-        if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        h->tune_ms[prec][2 * c16 + rpl - 1] = ms / 5.0;
-        if (ms / 5.0 < best_ms) {
-          best_ms = ms / 5.0;
+        double ms = 0.0;
+        time_kernel(prec, &ms);
+        h->tune_ms[prec][2 * c16 + rpl - 1] = ms;
+        if (ms < best_ms) {
+          best_ms = ms;
           best_rpl = rpl;
           best_c16 = c16;
         }
       }
     rpl_ref = best_rpl;
     c16_ref = best_c16;
+    if (prec == 1) best_sell32 = best_ms;
+  }
+  if (e == cudaSuccess && mixed && h->have_box && h->opts.fp32_operator == 0) {
+    h->d.t32 = 1;
+    time_kernel(1, &h->tune_tensor_ms);
+    h->d.t32 = 0;
+    if (e == cudaSuccess && h->tune_tensor_ms < best_sell32) h->fp32_tuned = 2;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   OSM_CUDA(h, e);
-  return OSM_OK;
+  // the tensor kernel's profiling run wrote its layout's p, q: start clean
+  if (h->have_box) {
+    const size_t n32 = std::max<size_t>((size_t)h->hp.vec_rows, (size_t)h->hp.box_rows);
+    for (float* v : {h->d.p32, h->d.q32}) OSM_CUDA(h, cudaMemsetAsync(v, 0, sizeof(float) * n32, h->stream));
+  }
+  return select_fp32_operator(h);
 }
 
 // Graph of the subdomain solves alone (x = A_i^-1 b_i from the current x):
@@ -735,7 +835,8 @@ osm_status osm_setup(const osm_mesh* mesh, const double* drho, const osm_decomp*
   osm_ctx* h = new (std::nothrow) osm_ctx();
   if (!h) return OSM_E_NOMEM;
   if (opts) h->opts = *opts; else osm_default_opts(&h->opts);
-  if (!(h->opts.inner_rtol > 0.0) || h->opts.max_outer < 1 || h->opts.max_inner < 1 || h->opts.max_seconds < 1) {
+  if (!(h->opts.inner_rtol > 0.0) || h->opts.max_outer < 1 || h->opts.max_inner < 1 || h->opts.max_seconds < 1 ||
+      h->opts.fp32_operator < 0 || h->opts.fp32_operator > 2) {
     delete h;
     return OSM_E_ARG;
   }
@@ -798,6 +899,10 @@ osm_status osm_info(osm_handle h, osm_info_t* o) {
   }
   o->col_bytes_fp64 = h->d.c16_64 ? 2 : 4;
   o->col_bytes_fp32 = h->opts.prec == OSM_MIXED ? (h->d.c16_32 ? 2 : 4) : 0;
+  o->fp32_operator = h->opts.prec == OSM_MIXED ? (h->d.t32 ? 2 : 1) : 0;
+  o->fp32_operator_tuned = h->opts.prec == OSM_MIXED ? h->fp32_tuned : 0;
+  o->tensor_ms_fp32 = h->tune_tensor_ms;
+  o->box_rows = h->have_box ? h->hp.box_rows : 0;
   return OSM_OK;
 }
 
@@ -889,7 +994,8 @@ osm_status osm_setup_batch(int32_t n_inst, const osm_mesh* meshes, const double*
   *out = h;
   if (!(h->opts.inner_rtol > 0.0) || h->opts.max_outer < 1 || h->opts.max_inner < 1 || h->opts.max_seconds < 1 ||
       (h->opts.prec != OSM_FP64 && h->opts.prec != OSM_MIXED && h->opts.prec != OSM_FP64_REFINE) ||
-      (h->opts.prec != OSM_FP64 && !(h->opts.mixed_inner_rtol > 0.0 && h->opts.mixed_inner_rtol < 1.0)))
+      (h->opts.prec != OSM_FP64 && !(h->opts.mixed_inner_rtol > 0.0 && h->opts.mixed_inner_rtol < 1.0)) ||
+      h->opts.fp32_operator < 0 || h->opts.fp32_operator > 2)
     return fail(h, OSM_E_ARG, "osm_setup_batch: bad options");
   h->stream = (cudaStream_t)cuda_stream;
   auto t0 = std::chrono::steady_clock::now();
@@ -1515,12 +1621,7 @@ osm_status osm_profile_spmv(osm_handle h, int32_t prec, int32_t reps, double* ms
 
 void osm_destroy(osm_handle h) {
   if (!h) return;
-  if (h->exec) cudaGraphExecDestroy(h->exec);
-  if (h->graph) cudaGraphDestroy(h->graph);
-  if (h->mp_exec) cudaGraphExecDestroy(h->mp_exec);
-  if (h->mp_graph) cudaGraphDestroy(h->mp_graph);
-  if (h->ls_exec) cudaGraphExecDestroy(h->ls_exec);
-  if (h->ls_graph) cudaGraphDestroy(h->ls_graph);
+  drop_graphs(h);
   cudaStreamSynchronize(h->stream);
   for (void* p : h->allocs) cudaFree(p);
   if (h->ctl_host) cudaFreeHost(h->ctl_host);

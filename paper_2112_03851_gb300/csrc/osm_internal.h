@@ -24,6 +24,9 @@ constexpr int kResFinThreads = 1024;
 // SELL row widths are padded to a multiple of 4 so that every lane can load
 // four column indices (int4) and two value pairs (double2) per step.
 constexpr int kWidthQuantum = 4;
+// Widest subdomain box (nodes along x) the tensor-product kernel stages in
+// shared memory; wider handles keep the SELL operator for the FP32 solve.
+constexpr int kTensorMaxNx = 128;
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kGravity = 6.672e-11;  // Sec. 2
@@ -41,6 +44,9 @@ struct SubInfo {
   int64_t tile0;                      // first tile
   int64_t slice0;                     // first slice
   bool iface[6];                      // -x, +x, -y, +y, -z, +z side is an interface
+  int32_t band0 = 0;                  // first node of its 1-D bands (x, then y, then z)
+  int32_t fmask = 0;                  // bits 0-5: side -x .. +z on the outer (Dirichlet)
+                                      // boundary; bits 8-13: side is an interface
 };
 
 // Everything the host builds before upload.
@@ -98,6 +104,27 @@ struct HostProblem {
   std::vector<double> fm_val;
   std::vector<double> fs_val;         // face tangential stiffness, same CSR
 
+  // Tensor-product form of the subdomain operators (mixed handles): the
+  // assembled 1-D Q2 stiffness and mass of every subdomain along x, y and z,
+  // 5 band entries per node (neighbours a-2 .. a+2), and the box index
+  // (i + bnx (j + bny k), box-local) of every vector row (-1: padding row).
+  std::vector<double> band_k, band_m;
+  std::vector<int32_t> row_boxidx;
+  // Box layout of the FP32 inner solve (build_box_layout): subdomain s's box
+  // node (i, j, k) at row box_voff[s] + i + bnx (j + bny k), each subdomain
+  // padded to whole 256-row tiles; the tensor kernel runs one CTA per 256
+  // (x, y) columns of a box.
+  std::vector<int64_t> box_voff;
+  std::vector<int32_t> box_dims;      // 4 per subdomain: bnx, bny, bnz, fmask
+  std::vector<int32_t> box_tile_sub;
+  std::vector<int64_t> box_sub_tile0; // n_sub + 1
+  std::vector<int64_t> box_ub_tile0;  // FP32 update blocks (kUpdGroup tiles of one subdomain)
+  std::vector<int32_t> box_cta_sub;
+  std::vector<int64_t> box_sub_cta0;  // n_sub + 1
+  std::vector<int32_t> row_box;       // vector row -> box row (-1: padding)
+  int64_t box_rows = 0, box_tiles = 0, box_ctas = 0;
+  int32_t box_max_nx = 0;
+
   // Copies of each node of the full grid (vector rows, subdomain order).
   std::vector<int32_t> cp_ptr;        // n_nodes + 1
   std::vector<int32_t> cp_idx;
@@ -126,6 +153,10 @@ void single_instance_tables(HostProblem& hp);
 // the reason of the failure.
 std::string build_host_problem(const osm_mesh& mesh, const double* drho, const osm_decomp& dec,
                                HostProblem& hp, bool want_fp32 = false);
+
+// Box layout tables of the tensor-product FP32 operator (from sub, band0,
+// row_boxidx and tile_sub).
+void build_box_layout(HostProblem& hp);
 
 // Rebuild the load vector (per vector row) for a new density.
 void build_load(const HostProblem& hp, const double* drho, std::vector<double>& f);
@@ -232,6 +263,26 @@ struct DevProblem {
   float* vals32;
   const int64_t* im_pos32;
   float *x32, *r32, *z32, *p32, *q32, *dinv32;
+  // Range table of the p.q partials of the CG step's SpMV kernel (sub_tile0
+  // for the SELL kernels; sub_cta0 for the tensor kernel).
+  const int64_t* sub_part0;
+  // FP32 inner solve on the tensor-product operator in the box layout (t32 =
+  // 1; else the FP32 SELL operator in the vector-row layout).  The x32 .. q32
+  // vectors then hold box rows, dinv32b is the box-layout Jacobi diagonal.
+  int32_t t32;
+  const int32_t* row_box;
+  const int64_t* box_voff;
+  const int32_t* box_dims;
+  const int32_t* box_band0;
+  const int32_t* box_tile_sub;
+  const int64_t* box_sub_tile0;
+  const int64_t* box_ub_tile0;
+  int64_t box_n_tiles, box_n_ublocks, n_cta32;
+  const int32_t* cta_sub;
+  const int64_t* sub_cta0;
+  const double *band_k, *band_m;        // plain 1-D bands (5 per band node)
+  float *cK32, *cM32;                   // FP32 bands, stiffness with the Robin terms folded in
+  float* dinv32b;
   DevCtl* ctl;
   const int32_t* can2vec;
   int64_t n_local;
@@ -313,6 +364,13 @@ cudaError_t launch_mixed_correct(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_apply32(const DevProblem& d, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_spmv_plain32(const DevProblem& d, const float* x, float* y, cudaStream_t s);
 cudaError_t launch_exchange(const DevProblem& d, cudaStream_t s);
+// tensor-product FP32 operator (osm_tensor.cu)
+cudaError_t launch_tensor_coef(const DevProblem& d, cudaStream_t s);
+cudaError_t launch_tensor_dir32(const DevProblem& d, cudaStream_t s);
+cudaError_t launch_tensor_apply32(const DevProblem& d, const float* x, float* y, cudaStream_t s);
+// The DevProblem seen by the FP32 CG kernels: the box layout's tile tables
+// when the tensor operator is in use, else d itself.
+DevProblem fp32_view(const DevProblem& d);
 // adjoint gradient (osm_adjoint.cu)
 cudaError_t launch_load_from_density(const DevProblem& d, const DevAdjoint& a, const double* drho, cudaStream_t s);
 cudaError_t launch_station_values(const DevProblem& d, const DevAdjoint& a, const double* phi, const double* g_obs,

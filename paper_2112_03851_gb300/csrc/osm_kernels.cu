@@ -49,6 +49,7 @@ __global__ void k_set_robin(DevProblem d) {
   const double di = 1.0 / (d.kdiag[row] + tc_term(c, d.irow_tdiag + 4 * (int64_t)k));
   d.dinv[row] = di;
   if (d.dinv32) d.dinv32[row] = (float)di;
+  if (d.dinv32b) d.dinv32b[d.row_box[row]] = (float)di;   // box layout of the tensor form
 }
 
 // b_i = f_i + sum_j lam_ij on interface rows (other rows keep b = f).
@@ -207,7 +208,8 @@ __device__ __forceinline__ void cg_step_finish(DevProblem& d, int s, int lane) {
   const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
   const double rz = warp_sum_parts(d.part1, t0, nt);
   const double rr = warp_sum_parts(d.part2, t0, nt);
-  const double pq = warp_sum_parts(d.part0, t0, nt);
+  const int64_t c0 = d.sub_part0[s];
+  const double pq = warp_sum_parts(d.part0, c0, d.sub_part0[s + 1] - c0);
   if (lane == 0) {
     const int it = d.st.iters[s] + 1;
     d.st.iters[s] = it;
@@ -337,7 +339,8 @@ __global__ void __launch_bounds__(kTileRows) k_cg_update_a(DevProblem d, CgVec<T
     }
   }
   if (warp == 0) {
-    const double pq = warp_sum_parts(d.part0, ts0, d.sub_tile0[s + 1] - ts0);
+    const int64_t c0 = d.sub_part0[s];
+    const double pq = warp_sum_parts(d.part0, c0, d.sub_part0[s + 1] - c0);
     if (lane == 0) s_alpha = (pq > 0.0 && isfinite(pq)) ? (T)(d.st.rho[s] / pq) : T(0);
   }
   __syncthreads();
@@ -453,10 +456,15 @@ __global__ void __launch_bounds__(kTileRows) k_cg_init_mixed(DevProblem d) {
     const double b = d.b[row[k]];
     const double dfc = b - ax[k];
     const float r = (float)dfc;
-    const float z = d.dinv32[row[k]] * r;
-    d.r32[row[k]] = r;
-    d.z32[row[k]] = z;   // p = z is formed by the first k_cg_spmv_dir32 (beta = 0)
-    d.x32[row[k]] = 0.f;
+    float z = 0.f;
+    // the FP32 solve's row: the same row, or its row in the tensor form's box layout
+    const int64_t rb = d.t32 ? (int64_t)d.row_box[row[k]] : row[k];
+    if (rb >= 0) {
+      z = (d.t32 ? d.dinv32b : d.dinv32)[rb] * r;
+      d.r32[rb] = r;
+      d.z32[rb] = z;   // p = z is formed by the first CG-step kernel (beta = 0)
+      d.x32[rb] = 0.f;
+    }
     vv[0] += dfc * dfc;
     vv[1] += b * b;
     vv[2] += (double)r * (double)z;
@@ -469,10 +477,16 @@ __global__ void __launch_bounds__(kTileRows) k_cg_init_mixed(DevProblem d) {
   }
 }
 
-// Mixed precision, end of the refinement step: u += e in FP64.
+// Mixed precision, end of the refinement step: u += e in FP64 (e read from
+// the tensor form's box layout when that is in use).
 __global__ void __launch_bounds__(kTileRows) k_mixed_correct(DevProblem d) {
   const int64_t row = blockIdx.x * (int64_t)kTileRows + threadIdx.x;
-  d.x[row] += (double)d.x32[row];
+  if (d.t32) {
+    const int32_t rb = d.row_box[row];
+    if (rb >= 0) d.x[row] += (double)d.x32[rb];
+  } else {
+    d.x[row] += (double)d.x32[row];
+  }
 }
 
 // y32 = A32 x32 (FP32 values) on every tile: the mixed inner operator.
@@ -488,16 +502,22 @@ __global__ void __launch_bounds__(kTileRows) k_spmv_plain32(DevProblem d, const 
   for (int k = 0; k < RPL; ++k) y[row[k]] = q[k];
 }
 
+// Canonical local layout <-> the FP32 solve's rows (box rows under the tensor form).
+__device__ __forceinline__ int64_t row32_of(const DevProblem& d, int64_t k) {
+  const int32_t r = d.can2vec[k];
+  return d.t32 ? (int64_t)d.row_box[r] : (int64_t)r;
+}
+
 __global__ void k_scatter_local32(DevProblem d, const double* __restrict__ canon, float* __restrict__ vec) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= d.n_local) return;
-  vec[d.can2vec[k]] = (float)canon[k];
+  vec[row32_of(d, k)] = (float)canon[k];
 }
 
 __global__ void k_gather_local32(DevProblem d, const float* __restrict__ vec, double* __restrict__ canon) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= d.n_local) return;
-  canon[k] = (double)vec[d.can2vec[k]];
+  canon[k] = (double)vec[row32_of(d, k)];
 }
 
 // Robin exchange on every face entry (parallel update, Sec. 3):
@@ -739,6 +759,14 @@ cudaError_t launch_cg_iteration(const DevProblem& d, cudaStream_t s, unsigned lo
 }
 
 cudaError_t launch_cg_iteration32(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
+  if (d.t32) {
+    const DevProblem b = fp32_view(d);
+    cudaError_t e = launch_tensor_dir32(b, s);
+    if (e != cudaSuccess) return e;
+    const CgVec<float> v{b.x32, b.r32, b.z32, b.p32, b.q32, b.dinv32b, b.vals32};
+    k_cg_update_a<float, kUpdGroup><<<(unsigned)b.n_ublocks, kTileRows, 0, s>>>(b, v, cond, use_cond);
+    return cudaGetLastError();
+  }
   OSM_LAUNCH_RPL(d.rpl32, d.c16_32, k_cg_spmv_dir32, s, d);
   const CgVec<float> v{d.x32, d.r32, d.z32, d.p32, d.q32, d.dinv32, d.vals32};
   k_cg_update_a<float, kUpdGroup><<<(unsigned)d.n_ublocks, kTileRows, 0, s>>>(d, v, cond, use_cond);
@@ -746,6 +774,7 @@ cudaError_t launch_cg_iteration32(const DevProblem& d, cudaStream_t s, unsigned 
 }
 
 cudaError_t launch_cg_spmv_alone(const DevProblem& d, int fp32, cudaStream_t s) {
+  if (fp32 && d.t32) return launch_tensor_dir32(fp32_view(d), s);
   if (fp32) {
     OSM_LAUNCH_RPL(d.rpl32, d.c16_32, k_cg_spmv_dir32, s, d);
   } else {
@@ -778,13 +807,15 @@ cudaError_t launch_mixed_correct(const DevProblem& d, cudaStream_t s) {
 }
 
 cudaError_t launch_spmv_plain32(const DevProblem& d, const float* x, float* y, cudaStream_t s) {
+  if (d.t32) return launch_tensor_apply32(d, x, y, s);
   OSM_LAUNCH_RPL(d.rpl32, d.c16_32, k_spmv_plain32, s, d, x, y);
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply32(const DevProblem& d, const double* x, double* y, cudaStream_t s) {
   k_scatter_local32<<<blocks_for(d.n_local, 256), 256, 0, s>>>(d, x, d.z32);
-  OSM_LAUNCH_RPL(d.rpl32, d.c16_32, k_spmv_plain32, s, d, d.z32, d.q32);
+  cudaError_t e = launch_spmv_plain32(d, d.z32, d.q32, s);
+  if (e != cudaSuccess) return e;
   k_gather_local32<<<blocks_for(d.n_local, 256), 256, 0, s>>>(d, d.q32, y);
   return cudaGetLastError();
 }

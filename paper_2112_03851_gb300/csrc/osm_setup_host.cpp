@@ -151,6 +151,10 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
     S.iface[0] = a > 0; S.iface[1] = a < hp.sx - 1;
     S.iface[2] = b > 0; S.iface[3] = b < hp.sy - 1;
     S.iface[4] = c > 0; S.iface[5] = c < hp.sz - 1;
+    S.fmask = (S.i0 == 0 ? 1 : 0) | (S.i1 == hp.NX - 1 ? 2 : 0) | (S.j0 == 0 ? 4 : 0) |
+              (S.j1 == hp.NY - 1 ? 8 : 0) | (S.k0 == 0 ? 16 : 0) | (S.k1 == hp.NZ - 1 ? 32 : 0);
+    for (int f = 0; f < 6; ++f)
+      if (S.iface[f]) S.fmask |= 1 << (8 + f);
     SubWork& w = W[s];
     w.bx.build(hp.xc, S.ex0, S.ex1);
     w.by.build(hp.yc, S.ey0, S.ey1);
@@ -240,6 +244,28 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
   for (int s = 0; s < nsub; ++s)
     for (int32_t q = 0; q < hp.sub[s].n; ++q)
       hp.can2vec[hp.sub[s].canon_off + q] = (int32_t)(hp.sub[s].voff + W[s].can2int[q]);
+  // tensor-product form (mixed handles): the 1-D bands of every subdomain and
+  // the box index of every vector row
+  hp.band_k.clear();
+  hp.band_m.clear();
+  hp.row_boxidx.clear();
+  if (want_fp32) {
+    hp.row_boxidx.assign(hp.vec_rows, -1);
+    for (int s = 0; s < nsub; ++s) {
+      SubInfo& S = hp.sub[s];
+      const SubWork& w = W[s];
+      S.band0 = (int32_t)(hp.band_k.size() / 5);
+      for (const Band1D* b : {&w.bx, &w.by, &w.bz}) {
+        hp.band_k.insert(hp.band_k.end(), b->K.begin(), b->K.end());
+        hp.band_m.insert(hp.band_m.end(), b->M.begin(), b->M.end());
+      }
+      for (int32_t q = 0; q < S.n; ++q) {
+        const int node = w.can_node[q];
+        const int i = node % hp.NX, j = (node / hp.NX) % hp.NY, k = node / (hp.NX * hp.NY);
+        hp.row_boxidx[S.voff + w.can2int[q]] = (i - S.i0) + w.bnx * ((j - S.j0) + w.bny * (k - S.k0));
+      }
+    }
+  }
 
   // ---- pass 2: fill SELL values and the Robin (interface) entries
   struct IfaceRow {
@@ -497,6 +523,50 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
   return std::string();
 }
 
+void build_box_layout(HostProblem& hp) {
+  const int ns = hp.nsub;
+  hp.box_voff.assign(ns, 0);
+  hp.box_dims.assign(4 * (size_t)ns, 0);
+  hp.box_tile_sub.clear();
+  hp.box_sub_tile0.assign(ns + 1, 0);
+  hp.box_ub_tile0.clear();
+  hp.box_cta_sub.clear();
+  hp.box_sub_cta0.assign(ns + 1, 0);
+  hp.box_max_nx = 0;
+  int64_t rows = 0, tiles = 0, ctas = 0;
+  for (int s = 0; s < ns; ++s) {
+    const SubInfo& S = hp.sub[s];
+    const int bnx = S.i1 - S.i0 + 1, bny = S.j1 - S.j0 + 1, bnz = S.k1 - S.k0 + 1;
+    hp.box_dims[4 * s + 0] = bnx;
+    hp.box_dims[4 * s + 1] = bny;
+    hp.box_dims[4 * s + 2] = bnz;
+    hp.box_dims[4 * s + 3] = S.fmask;
+    hp.box_max_nx = std::max(hp.box_max_nx, bnx);
+    const int64_t nb = (int64_t)bnx * bny * bnz;
+    const int64_t nt = std::max<int64_t>(1, (nb + kTileRows - 1) / kTileRows);
+    hp.box_voff[s] = rows;
+    hp.box_sub_tile0[s] = tiles;
+    for (int64_t t = 0; t < nt; ++t) hp.box_tile_sub.push_back(s);
+    for (int64_t t = 0; t < nt; t += kUpdGroup) hp.box_ub_tile0.push_back(tiles + t);
+    rows += nt * kTileRows;
+    tiles += nt;
+    const int64_t nc = ((int64_t)bnx * bny + kTileRows - 1) / kTileRows;
+    hp.box_sub_cta0[s] = ctas;
+    for (int64_t c = 0; c < nc; ++c) hp.box_cta_sub.push_back(s);
+    ctas += nc;
+  }
+  hp.box_sub_tile0[ns] = tiles;
+  hp.box_sub_cta0[ns] = ctas;
+  hp.box_rows = rows;
+  hp.box_tiles = tiles;
+  hp.box_ctas = ctas;
+  hp.row_box.assign(hp.vec_rows, -1);
+  for (int64_t r = 0; r < hp.vec_rows; ++r) {
+    const int32_t b = hp.row_boxidx[r];
+    if (b >= 0) hp.row_box[r] = (int32_t)(hp.box_voff[hp.tile_sub[r / kTileRows]] + b);
+  }
+}
+
 // Residual blocks of nodes [n0, n1) of instance `inst`: about one block per
 // 256 nodes (one per thread of a 256-thread block), at least one.
 static void add_rblocks(HostProblem& hp, int inst, int64_t n0, int64_t n1) {
@@ -558,10 +628,15 @@ std::string merge_problems(std::vector<HostProblem>& parts, HostProblem& out) {
     if (vec_off + p.vec_rows >= ((int64_t)1 << 31) || node_off + p.n_nodes >= ((int64_t)1 << 31) ||
         fm_off + (int64_t)p.fm_col.size() >= ((int64_t)1 << 31))
       return "batched problem too large for 32-bit indices";
+    const int32_t band_off = (int32_t)(o.band_k.size() / 5);
     for (SubInfo S : p.sub) {
       S.voff += vec_off; S.canon_off += canon_off; S.tile0 += tile_off; S.slice0 += slice_off;
+      S.band0 += band_off;
       o.sub.push_back(S);
     }
+    append(o.band_k, p.band_k);
+    append(o.band_m, p.band_m);
+    append(o.row_boxidx, p.row_boxidx);
     for (int64_t k = 0; k < p.n_slices; ++k) o.slice_off.push_back(p.slice_off[k] + ent_off);
     append(o.cols, p.cols);
     append(o.vals, p.vals);

@@ -1,0 +1,257 @@
+// Matrix-free FP32 subdomain operator of the mixed inner solve.
+//
+// On an axis-aligned tensor-product mesh the Q2 Neumann stiffness of a box of
+// elements is exactly
+//     K_i = Kx (x) My (x) Mz + Mx (x) Ky (x) Mz + Mx (x) My (x) Kz
+// with Kx, Mx the assembled 1-D Q2 stiffness and mass along x (banded: node a
+// couples with a-2 .. a+2), and the Robin term of a face, p M_G = p E (x) My
+// (x) Mz for a face normal to x (E: the unit entry at the face's end node),
+// folds into the 1-D stiffness: (Kx + p E) (x) My (x) Mz.  So
+//     A_i = K~x (x) My (x) Mz + Mx (x) K~y (x) Mz + Mx (x) My (x) K~z
+// for the zeroth-order transmission condition of Sec. 3 (q = 0; the second-
+// order term q S_G does not factor this way and keeps the SELL matrix).
+//
+// The kernel applies A_i by sum factorisation without reading any matrix.
+// A CTA owns 256 consecutive (x, y) columns of one subdomain box and marches
+// along z.  Every input plane is staged in shared memory with two rows of
+// halo in y; the y pass forms My z and Ky z, the x pass the plane's two
+// partial products P = (K~x (x) My + Mx (x) K~y) z and Q = (Mx (x) My) z, and
+// each thread keeps P and Q of the last five planes in registers, so that
+// output plane k = sum_c Mz(k, c) P(k+c-2) + K~z(k, c) Q(k+c-2).  About 36
+// FMAs and two staged loads per row replace the 62 values and column indices
+// (8 bytes each) the SELL SpMV streams from HBM.
+//
+// Layout ("box layout"): subdomain s's box node (i, j, k) -- Dirichlet nodes
+// of the outer boundary included, held at zero -- is row box_voff[s] + i +
+// bnx (j + bny k).  Rows on the outer boundary are written as zero.
+#include <cuda_runtime.h>
+
+#include "osm_device.cuh"
+#include "osm_internal.h"
+
+namespace osm {
+
+namespace {
+
+constexpr int kTxPlane = kTileRows + 6 * kTensorMaxNx;   // staged input plane: CTA rows + 4 halo rows
+constexpr int kTxRows = kTileRows + 2 * kTensorMaxNx;    // y-pass outputs: the CTA's rows, all x
+constexpr int kTxPre = (kTxPlane + kTileRows - 1) / kTileRows;
+constexpr int kTxY = (kTxRows + kTileRows - 1) / kTileRows;
+
+// FP32 bands of every subdomain: the mass as it is, the stiffness with the
+// transmission term p of each interface side added at that side's end node
+// (a subdomain uses p_lo on the faces where it is the lower side -- its +x,
+// +y, +z sides -- and p_hi on its -x, -y, -z sides).  One block per subdomain.
+__global__ void k_tensor_coef(DevProblem d) {
+  const int s = blockIdx.x;
+  const int* dims = d.box_dims + 4 * s;
+  const int nx = dims[0], ny = dims[1], nz = dims[2], fm = dims[3];
+  const double* c = d.tc + 4 * s;
+  const int64_t b0 = (int64_t)d.box_band0[s] * 5;
+  const int n5 = 5 * (nx + ny + nz);
+  for (int t = threadIdx.x; t < n5; t += blockDim.x) {
+    double kv = d.band_k[b0 + t];
+    const double mv = d.band_m[b0 + t];
+    if (t % 5 == 2) {   // diagonal entry of band node t / 5
+      const int node = t / 5;
+      const int ax = node < nx ? 0 : (node < nx + ny ? 1 : 2);
+      const int pos = ax == 0 ? node : (ax == 1 ? node - nx : node - nx - ny);
+      const int len = ax == 0 ? nx : (ax == 1 ? ny : nz);
+      if (pos == 0 && ((fm >> (8 + 2 * ax)) & 1)) kv += c[2];
+      if (pos == len - 1 && ((fm >> (9 + 2 * ax)) & 1)) kv += c[0];
+    }
+    d.cK32[b0 + t] = (float)kv;
+    d.cM32[b0 + t] = (float)mv;
+  }
+}
+
+// MODE 0: one step of the FP32 inner CG (the tensor counterpart of
+// k_cg_spmv_dir32): t = A z, then p = z + beta p, q = t + beta q (first step
+// beta = 0: p = z, q = t) and the CTA's partial of p.q (scaled FP32 dots as in
+// the SELL kernel) into part0[cta].  MODE 1: y = A x (x, y in the box layout).
+template <int MODE>
+__global__ void __launch_bounds__(kTileRows) k_tensor32(DevProblem d, const float* __restrict__ xin,
+                                                        float* __restrict__ yout) {
+  __shared__ float S[2][kTxPlane];
+  __shared__ float TM[kTxRows], TK[kTxRows];
+  __shared__ double red[kTileSlices];
+  const int cta = blockIdx.x;
+  const int s = d.cta_sub[cta];
+  if (MODE == 0 && !d.st.active[s]) return;
+  const int* dims = d.box_dims + 4 * s;
+  const int nx = dims[0], ny = dims[1], nz = dims[2], fm = dims[3];
+  const int nxy = nx * ny;
+  const int64_t voff = d.box_voff[s];
+  const int c0 = (int)(cta - d.sub_cta0[s]) * kTileRows;
+  const int col = c0 + (int)threadIdx.x;
+  const bool valid = col < nxy;
+  const int jlo = c0 / nx, jhi = min(ny - 1, (c0 + kTileRows - 1) / nx);
+  const int nrow = jhi - jlo + 1, nload = (nrow + 4) * nx, ntr = nrow * nx;
+  const int j = valid ? col / nx : jlo, i = valid ? col - j * nx : 0;
+  const int64_t bx = (int64_t)d.box_band0[s] * 5, by = bx + 5 * (int64_t)nx, bz = by + 5 * (int64_t)ny;
+  const float* __restrict__ cK = d.cK32;
+  const float* __restrict__ cM = d.cM32;
+  float kx[5], mx[5];
+#pragma unroll
+  for (int a = 0; a < 5; ++a) {
+    kx[a] = cK[bx + 5 * i + a];
+    mx[a] = cM[bx + 5 * i + a];
+  }
+  // column on the outer boundary (x or y side): its rows are Dirichlet
+  const bool dcol = ((fm & 1) && i == 0) || ((fm & 2) && i == nx - 1) || ((fm & 4) && j == 0) ||
+                    ((fm & 8) && j == ny - 1);
+  // plane-relative offsets of this thread's staged values (the same in every plane)
+  int goff[kTxPre];
+#pragma unroll
+  for (int m = 0; m < kTxPre; ++m) {
+    const int idx = (int)threadIdx.x + m * kTileRows;
+    goff[m] = -1;
+    if (idx < nload) {
+      const int r = idx / nx, jj = jlo - 2 + r;
+      if (jj >= 0 && jj < ny) goff[m] = (idx - r * nx) + nx * jj;
+    }
+  }
+  int yrow[kTxY];
+#pragma unroll
+  for (int m = 0; m < kTxY; ++m) {
+    const int idx = (int)threadIdx.x + m * kTileRows;
+    yrow[m] = idx < ntr ? idx / nx : -1;
+  }
+  const float* __restrict__ src = MODE == 0 ? d.z32 : xin;
+  float pre[kTxPre];
+  auto fetch = [&](int kk) {
+    const bool in = kk >= 0 && kk < nz;
+    const int64_t pl = voff + (int64_t)nxy * kk;
+#pragma unroll
+    for (int m = 0; m < kTxPre; ++m) pre[m] = (in && goff[m] >= 0) ? src[pl + goff[m]] : 0.f;
+  };
+  float beta = 0.f, sc = 1.f;
+  bool first = true;
+  if (MODE == 0) {
+    const double b64 = d.st.beta[s];
+    first = b64 == 0.0;
+    beta = (float)b64;
+    sc = d.st.sc[s];
+  }
+  float ph[5], qh[5], zh[5];
+#pragma unroll
+  for (int c = 0; c < 5; ++c) { ph[c] = 0.f; qh[c] = 0.f; zh[c] = 0.f; }
+  float vv = 0.f;
+  fetch(-2);
+  int buf = 0;
+  for (int kk = -2; kk < nz + 2; ++kk) {
+#pragma unroll
+    for (int m = 0; m < kTxPre; ++m) {
+      const int idx = (int)threadIdx.x + m * kTileRows;
+      if (idx < nload) S[buf][idx] = pre[m];
+    }
+    __syncthreads();
+    if (kk + 1 < nz + 2) fetch(kk + 1);   // the next plane's loads overlap this plane's work
+    // y pass: My z and Ky z on the CTA's rows, every x
+#pragma unroll
+    for (int m = 0; m < kTxY; ++m) {
+      if (yrow[m] >= 0) {
+        const int idx = (int)threadIdx.x + m * kTileRows;
+        const int64_t cy = by + 5 * (int64_t)(jlo + yrow[m]);
+        float sm = 0.f, sk = 0.f;
+#pragma unroll
+        for (int b = 0; b < 5; ++b) {
+          const float v = S[buf][idx + b * nx];
+          sm = fmaf(cM[cy + b], v, sm);
+          sk = fmaf(cK[cy + b], v, sk);
+        }
+        TM[idx] = sm;
+        TK[idx] = sk;
+      }
+    }
+    __syncthreads();
+    // x pass for this thread's column: P = K~x (My z) + Mx (K~y z), Q = Mx (My z)
+    float P = 0.f, Q = 0.f, zc = 0.f;
+    if (valid) {
+      const int base = (j - jlo) * nx + i;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        const int ii = i + a - 2;
+        if (ii >= 0 && ii < nx) {
+          const float tm = TM[base + a - 2], tk = TK[base + a - 2];
+          P = fmaf(kx[a], tm, fmaf(mx[a], tk, P));
+          Q = fmaf(mx[a], tm, Q);
+        }
+      }
+      zc = S[buf][base + 2 * nx];
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { ph[c] = ph[c + 1]; qh[c] = qh[c + 1]; zh[c] = zh[c + 1]; }
+    ph[4] = P;
+    qh[4] = Q;
+    zh[4] = zc;
+    const int k = kk - 2;   // output plane: its neighbours k-2 .. k+2 are in the rings
+    if (valid && k >= 0) {
+      const int64_t cz = bz + 5 * (int64_t)k;
+      float t = 0.f;
+#pragma unroll
+      for (int c = 0; c < 5; ++c) t = fmaf(cM[cz + c], ph[c], fmaf(cK[cz + c], qh[c], t));
+      if (dcol || ((fm & 16) && k == 0) || ((fm & 32) && k == nz - 1)) t = 0.f;
+      const int64_t row = voff + col + (int64_t)nxy * k;
+      if (MODE == 0) {
+        const float z = zh[2];
+        float p = z, q = t;
+        if (!first) {
+          p = fmaf(beta, d.p32[row], z);
+          q = fmaf(beta, d.q32[row], t);
+        }
+        d.p32[row] = p;
+        d.q32[row] = q;
+        vv = fmaf(p * sc, q * sc, vv);
+      } else {
+        yout[row] = t;
+      }
+    }
+    buf ^= 1;
+  }
+  if (MODE == 0) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, o);
+    if (lane == 0) red[warp] = (double)vv * d.st.isc2[s];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double acc = 0.0;
+#pragma unroll
+      for (int w = 0; w < kTileSlices; ++w) acc += red[w];
+      d.part0[cta] = acc;
+    }
+  }
+}
+
+}  // namespace
+
+DevProblem fp32_view(const DevProblem& d) {
+  if (!d.t32) return d;
+  DevProblem v = d;
+  v.tile_sub = d.box_tile_sub;
+  v.sub_tile0 = d.box_sub_tile0;
+  v.n_tiles = d.box_n_tiles;
+  v.ub_tile0 = d.box_ub_tile0;
+  v.n_ublocks = d.box_n_ublocks;
+  v.sub_part0 = d.sub_cta0;
+  return v;
+}
+
+cudaError_t launch_tensor_coef(const DevProblem& d, cudaStream_t s) {
+  if (!d.box_dims || d.n_sub == 0) return cudaSuccess;
+  k_tensor_coef<<<(unsigned)d.n_sub, 128, 0, s>>>(d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tensor_dir32(const DevProblem& d, cudaStream_t s) {
+  k_tensor32<0><<<(unsigned)d.n_cta32, kTileRows, 0, s>>>(d, nullptr, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tensor_apply32(const DevProblem& d, const float* x, float* y, cudaStream_t s) {
+  k_tensor32<1><<<(unsigned)d.n_cta32, kTileRows, 0, s>>>(d, x, y);
+  return cudaGetLastError();
+}
+
+}  // namespace osm

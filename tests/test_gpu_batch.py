@@ -29,10 +29,12 @@ def _instances():
     return [a, b, c, d]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_batch_equals_single_solves(osm, prec):
+@pytest.mark.parametrize("prec, fp32_op", [("fp64", 0), ("mixed", 1), ("mixed", 2)])
+def test_batch_equals_single_solves(osm, prec, fp32_op):
     probs = _instances()
-    kw = dict(prec=prec, inner_rtol=1e-13, max_outer=3000)
+    # the FP32 operator is pinned (SELL or tensor form): the autotuner could
+    # pick differently for the batch and for a single instance
+    kw = dict(prec=prec, inner_rtol=1e-13, max_outer=3000, fp32_operator=fp32_op)
     bs = osm.BatchSolver(probs, **kw)
     phi, iters, rel = bs.solve(rtol=1e-10)
     assert np.all(rel <= 1e-10)

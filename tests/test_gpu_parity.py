@@ -219,7 +219,8 @@ def test_spmv_variants_agree(osm):
     same solve up to reduction rounding."""
     import torch
     prob = small_uneven()
-    sols = [osm.Solver.from_problem(prob, p=2.0, autotune=a, prec="mixed", inner_rtol=1e-13) for a in (0, 2, 1)]
+    sols = [osm.Solver.from_problem(prob, p=2.0, autotune=a, prec="mixed", inner_rtol=1e-13, fp32_operator=1)
+            for a in (0, 2, 1)]
     assert sols[0].info["spmv_variant_fp64"] == 1 and sols[1].info["spmv_variant_fp64"] == 2
     assert sols[2].info["spmv_variant_fp64"] in (1, 2) and min(sols[2].info["spmv_ms_fp64"]) > 0
     rng = np.random.default_rng(1)

@@ -94,7 +94,10 @@ def test_sample_in_refinement_modes_matches_single_solves(osm, prec):
     (+-1 for rounding of the reductions) and a residual at rtol."""
     prob = small_uneven()
     ps = gen.log_uniform_p(3, 5, 0.5, 20.0)
-    sol = osm.Solver.from_problem(prob, prec=prec, mixed_inner_rtol=0.3, inner_rtol=1e-12, max_outer=1500)
+    # the batched evaluation's FP32 inner solve reads the SELL matrix: the
+    # single solves it is compared with use it too
+    sol = osm.Solver.from_problem(prob, prec=prec, mixed_inner_rtol=0.3, inner_rtol=1e-12, max_outer=1500,
+                                  fp32_operator=1)
     iters, rel, best = sol.sample_p(ps, rtol=1e-9, max_outer=1500)
     for k, p in enumerate(ps):
         sol.set_robin(float(p))
