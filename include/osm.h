@@ -148,8 +148,13 @@ typedef struct {
                                     product (0 without OSM_MIXED) */
     int32_t fp32_operator_tuned; /* the autotuner's (or opts.fp32_operator's) choice, used
                                     whenever the transmission condition allows it */
-    double tensor_ms_fp32;       /* autotuner timing of the tensor-product CG-step kernel
-                                    (ms, 0 if not run) */
+    double tensor_ms_fp32;       /* autotuner timing of the tensor-product CG-step kernel in its
+                                    chosen shape (ms, 0 if not run) */
+    int32_t tensor_zchunk;       /* z planes per CTA of the tensor kernel (0: no tensor form);
+                                    2^20 leaves every subdomain box whole */
+    int32_t reserved_i;
+    double tensor_ms_zchunk[4];  /* autotuner timings with z chunks of 8, 16, 32 planes and
+                                    whole boxes (ms, 0 if not run) */
     int64_t box_rows;            /* rows of the box layout of the tensor form (0 if none) */
 } osm_info_t;
 

@@ -55,7 +55,8 @@ class OsmInfo(C.Structure):
                 ("spmv_ms16_fp64", C.c_double * 2), ("spmv_ms16_fp32", C.c_double * 2),
                 ("col_bytes_fp64", C.c_int32), ("col_bytes_fp32", C.c_int32),
                 ("fp32_operator", C.c_int32), ("fp32_operator_tuned", C.c_int32),
-                ("tensor_ms_fp32", C.c_double), ("box_rows", C.c_int64)]
+                ("tensor_ms_fp32", C.c_double), ("tensor_zchunk", C.c_int32), ("reserved_i", C.c_int32),
+                ("tensor_ms_zchunk", C.c_double * 4), ("box_rows", C.c_int64)]
 
 
 def _info_dict(info):

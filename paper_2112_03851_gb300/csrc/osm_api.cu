@@ -27,6 +27,10 @@
 
 using namespace osm;
 
+// z-chunk lengths the autotuner tries for the tensor kernel (the last one
+// leaves every box whole).
+constexpr int kZChunks[4] = {8, 16, 32, 1 << 20};
+
 struct osm_ctx {
   HostProblem hp;
   osm_opts opts;
@@ -55,7 +59,9 @@ struct osm_ctx {
   // tensor-product FP32 operator (mixed handles whose boxes fit the kernel)
   bool have_box = false;
   int fp32_tuned = 1;           // 1: SELL, 2: tensor product (autotuner or opts.fp32_operator)
+  int zchunk = kZChunks[1];     // z planes per CTA of the tensor kernel (autotuned)
   double tune_tensor_ms = 0.0;
+  double tune_zchunk_ms[4] = {};
   // adjoint gradient (allocated on first use)
   bool adj_ready = false;
   DevAdjoint adj{};
@@ -102,6 +108,8 @@ cudaError_t upload(osm_ctx* h, T** p, const std::vector<T>& v) {
   return e;
 }
 
+cudaError_t set_zchunk(osm_ctx* h, int zc);
+
 osm_status upload_problem(osm_ctx* h) {
   HostProblem& hp = h->hp;
   DevProblem& d = h->d;
@@ -119,14 +127,18 @@ osm_status upload_problem(osm_ctx* h) {
   d.slice_off = slice_off; d.cols = cols; d.tile_sub = tile_sub; d.sub_tile0 = sub_tile0;
   // blocks of the FP32 CG update: runs of up to kUpdGroup tiles within a subdomain
   for (int g : {kUpdGroup, kUpdGroup64}) {
-    std::vector<int64_t> ub;
+    std::vector<int64_t> ub, sub_ub0(ns + 1, 0);
     for (size_t si = 0; si < ns; ++si) {
       const int64_t a0 = st0[si], a1 = st0[si + 1];
+      sub_ub0[si] = (int64_t)ub.size();
       for (int64_t t = a0; t < a1; t += g) ub.push_back(t);
     }
-    int64_t* dub;
+    sub_ub0[ns] = (int64_t)ub.size();
+    int64_t *dub, *dsub;
     OSM_CUDA(h, upload(h, &dub, ub));
+    OSM_CUDA(h, upload(h, &dsub, sub_ub0));
     (g == kUpdGroup ? d.ub_tile0 : d.ub64_tile0) = dub;
+    (g == kUpdGroup ? d.sub_ub0 : d.sub_ub64_0) = dsub;
     (g == kUpdGroup ? d.n_ublocks : d.n_ublocks64) = (int64_t)ub.size();
   }
   // 16-bit column indices for the single-path SpMVs when every subdomain fits
@@ -158,7 +170,7 @@ osm_status upload_problem(osm_ctx* h) {
   OSM_CUDA(h, dalloc(h, &st.isc2, ns));
   // the tensor form of the FP32 operator (mixed handles): box layout tables
   if (h->opts.prec == OSM_MIXED && h->opts.fp32_operator != 1 && !hp.row_boxidx.empty()) {
-    build_box_layout(hp);
+    build_box_layout(hp, kZChunks[0]);   // the smallest chunk: the most CTAs
     h->have_box = hp.box_max_nx <= kTensorMaxNx && hp.box_rows < ((int64_t)1 << 31);
   }
   const size_t nparts = h->have_box ? (size_t)std::max({hp.n_tiles, hp.box_tiles, hp.box_ctas}) : (size_t)hp.n_tiles;
@@ -258,6 +270,9 @@ osm_status upload_problem(osm_ctx* h) {
       OSM_CUDA(h, upload(h, &box_tile_sub, hp.box_tile_sub));
       OSM_CUDA(h, upload(h, &box_sub_tile0, hp.box_sub_tile0));
       OSM_CUDA(h, upload(h, &box_ub_tile0, hp.box_ub_tile0));
+      int64_t* box_sub_ub0;
+      OSM_CUDA(h, upload(h, &box_sub_ub0, hp.box_sub_ub0));
+      d.box_sub_ub0 = box_sub_ub0;
       OSM_CUDA(h, upload(h, &cta_sub, hp.box_cta_sub));
       OSM_CUDA(h, upload(h, &sub_cta0, hp.box_sub_cta0));
       d.row_box = row_box; d.box_voff = box_voff; d.box_dims = box_dims; d.box_band0 = box_band0;
@@ -266,6 +281,7 @@ osm_status upload_problem(osm_ctx* h) {
       d.box_n_tiles = hp.box_tiles;
       d.box_n_ublocks = (int64_t)hp.box_ub_tile0.size();
       d.n_cta32 = hp.box_ctas;
+      OSM_CUDA(h, set_zchunk(h, h->zchunk));
       double *bk, *bm;
       OSM_CUDA(h, upload(h, &bk, hp.band_k));
       OSM_CUDA(h, upload(h, &bm, hp.band_m));
@@ -286,6 +302,25 @@ osm_status upload_problem(osm_ctx* h) {
 // symmetric form, used by the batched p evaluation and the p-derivative) and
 // forms the local matrices and Jacobi diagonals.
 osm_status select_fp32_operator(osm_ctx* h);
+
+// CTA tables of the tensor kernel for z chunks of about `zc` planes, into the
+// device arrays sized for the smallest chunk.
+cudaError_t set_zchunk(osm_ctx* h, int zc) {
+  HostProblem& hp = h->hp;
+  box_cta_tables(hp, zc);
+  h->zchunk = zc;
+  cudaError_t e = cudaMemcpyAsync((void*)h->d.box_dims, hp.box_dims.data(), sizeof(int32_t) * hp.box_dims.size(),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((void*)h->d.cta_sub, hp.box_cta_sub.data(), sizeof(int32_t) * hp.box_cta_sub.size(),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((void*)h->d.sub_cta0, hp.box_sub_cta0.data(), sizeof(int64_t) * hp.box_sub_cta0.size(),
+                        cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);   // the host tables change on the next call
+  h->d.n_cta32 = hp.box_ctas;
+  return e;
+}
 
 osm_status apply_robin(osm_ctx* h) {
   OSM_CUDA(h, cudaMemcpyAsync(h->d.psub, h->psub_host.data(), sizeof(double) * h->hp.nsub,
@@ -556,11 +591,23 @@ osm_status autotune_spmv(osm_ctx* h) {
     c16_ref = best_c16;
     if (prec == 1) best_sell32 = best_ms;
   }
-  if (e == cudaSuccess && mixed && h->have_box && h->opts.fp32_operator == 0) {
+  if (e == cudaSuccess && mixed && h->have_box) {
+    // the tensor kernel with every z-chunk length; the fastest stays
     h->d.t32 = 1;
-    time_kernel(1, &h->tune_tensor_ms);
+    int best_zc = h->zchunk;
+    double best_t = 1e300;
+    for (int c = 0; c < 4 && e == cudaSuccess; ++c) {
+      e = set_zchunk(h, kZChunks[c]);
+      if (e == cudaSuccess) time_kernel(1, &h->tune_zchunk_ms[c]);
+      if (h->tune_zchunk_ms[c] < best_t) {
+        best_t = h->tune_zchunk_ms[c];
+        best_zc = kZChunks[c];
+      }
+    }
+    if (e == cudaSuccess) e = set_zchunk(h, best_zc);
+    h->tune_tensor_ms = best_t;
     h->d.t32 = 0;
-    if (e == cudaSuccess && h->tune_tensor_ms < best_sell32) h->fp32_tuned = 2;
+    if (e == cudaSuccess && h->opts.fp32_operator == 0 && best_t < best_sell32) h->fp32_tuned = 2;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -902,6 +949,8 @@ osm_status osm_info(osm_handle h, osm_info_t* o) {
   o->fp32_operator = h->opts.prec == OSM_MIXED ? (h->d.t32 ? 2 : 1) : 0;
   o->fp32_operator_tuned = h->opts.prec == OSM_MIXED ? h->fp32_tuned : 0;
   o->tensor_ms_fp32 = h->tune_tensor_ms;
+  o->tensor_zchunk = h->have_box ? h->zchunk : 0;
+  for (int c = 0; c < 4; ++c) o->tensor_ms_zchunk[c] = h->tune_zchunk_ms[c];
   o->box_rows = h->have_box ? h->hp.box_rows : 0;
   return OSM_OK;
 }

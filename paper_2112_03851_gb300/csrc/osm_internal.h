@@ -27,6 +27,9 @@ constexpr int kWidthQuantum = 4;
 // Widest subdomain box (nodes along x) the tensor-product kernel stages in
 // shared memory; wider handles keep the SELL operator for the FP32 solve.
 constexpr int kTensorMaxNx = 128;
+// Entries per subdomain of the box table: bnx, bny, bnz, face mask, z-chunk
+// length, column blocks, z chunks, unused.
+constexpr int kBoxDims = 8;
 
 constexpr double kPi = 3.14159265358979323846;
 constexpr double kGravity = 6.672e-11;  // Sec. 2
@@ -115,10 +118,11 @@ struct HostProblem {
   // padded to whole 256-row tiles; the tensor kernel runs one CTA per 256
   // (x, y) columns of a box.
   std::vector<int64_t> box_voff;
-  std::vector<int32_t> box_dims;      // 4 per subdomain: bnx, bny, bnz, fmask
+  std::vector<int32_t> box_dims;      // kBoxDims per subdomain (see kBoxDims)
   std::vector<int32_t> box_tile_sub;
   std::vector<int64_t> box_sub_tile0; // n_sub + 1
   std::vector<int64_t> box_ub_tile0;  // FP32 update blocks (kUpdGroup tiles of one subdomain)
+  std::vector<int64_t> box_sub_ub0;   // n_sub + 1: first update block of each subdomain
   std::vector<int32_t> box_cta_sub;
   std::vector<int64_t> box_sub_cta0;  // n_sub + 1
   std::vector<int32_t> row_box;       // vector row -> box row (-1: padding)
@@ -155,8 +159,12 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
                                HostProblem& hp, bool want_fp32 = false);
 
 // Box layout tables of the tensor-product FP32 operator (from sub, band0,
-// row_boxidx and tile_sub).
-void build_box_layout(HostProblem& hp);
+// row_boxidx and tile_sub); the tensor kernel's CTAs split each box's z
+// range into chunks of about zchunk planes.
+void build_box_layout(HostProblem& hp, int zchunk);
+// Only the CTA tables (box_dims chunk entries, box_cta_sub, box_sub_cta0)
+// for another z-chunk length.
+void box_cta_tables(HostProblem& hp, int zchunk);
 
 // Rebuild the load vector (per vector row) for a new density.
 void build_load(const HostProblem& hp, const double* drho, std::vector<double>& f);
@@ -213,6 +221,8 @@ struct DevProblem {
   int64_t n_ublocks;
   const int64_t* ub64_tile0;  // ... of each FP64-update block (kUpdGroup64 tiles)
   int64_t n_ublocks64;
+  const int64_t* sub_ub0;     // n_sub + 1: first FP32-update block of each subdomain
+  const int64_t* sub_ub64_0;  // n_sub + 1: first FP64-update block of each subdomain
   double* vals;
   const int32_t* tile_sub;
   const int64_t* sub_tile0;   // n_sub + 1
@@ -277,6 +287,7 @@ struct DevProblem {
   const int32_t* box_tile_sub;
   const int64_t* box_sub_tile0;
   const int64_t* box_ub_tile0;
+  const int64_t* box_sub_ub0;
   int64_t box_n_tiles, box_n_ublocks, n_cta32;
   const int32_t* cta_sub;
   const int64_t* sub_cta0;

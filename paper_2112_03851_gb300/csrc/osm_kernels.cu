@@ -201,13 +201,14 @@ __global__ void k_fin_init(DevProblem d, int mixed, unsigned long long cond, int
 
 // End of a CG step for subdomain s, by one warp (the finishing block of
 // k_cg_update_a): rho = r.z, the stop test ||r|| <= tau ||b|| (or the
-// iteration cap), beta, from the tile partials in a fixed order.  A
-// subdomain whose p.q partials (still in part0; k_cg_update_a left its
+// iteration cap), beta, from the partials in a fixed order (r.z and ||r||^2:
+// one per update block, [ub0[s], ub0[s+1]); p.q: one per tile or tensor CTA,
+// sub_part0).  A subdomain whose p.q partials (k_cg_update_a left its
 // iterate alone) sum to <= 0 stops with a breakdown.
-__device__ __forceinline__ void cg_step_finish(DevProblem& d, int s, int lane) {
-  const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
-  const double rz = warp_sum_parts(d.part1, t0, nt);
-  const double rr = warp_sum_parts(d.part2, t0, nt);
+__device__ __forceinline__ void cg_step_finish(DevProblem& d, const int64_t* __restrict__ ub0, int s, int lane) {
+  const int64_t b0 = ub0[s], nb = ub0[s + 1] - b0;
+  const double rz = warp_sum_parts(d.part1, b0, nb);
+  const double rr = warp_sum_parts(d.part2, b0, nb);
   const int64_t c0 = d.sub_part0[s];
   const double pq = warp_sum_parts(d.part0, c0, d.sub_part0[s + 1] - c0);
   if (lane == 0) {
@@ -299,26 +300,29 @@ __global__ void __launch_bounds__(kTileRows) k_cg_spmv_dir32(DevProblem d) {
 
 // alpha = rho / (p.q) (a breakdown, p.q <= 0, leaves the iterate alone and
 // the step's finish stops the subdomain), x += alpha p, r -= alpha q,
-// z = D^-1 r, and the tile partials of r.z and ||r||^2; the subdomain's last
-// block to finish then ends the step (cg_step_finish, cg_step_arrive).
-// A block covers up to
-// G consecutive tiles of one subdomain (d.ub_tile0 / d.ub64_tile0; FP32: 8,
-// FP64: 2, which keeps its registers, and so its occupancy, up): alpha is formed
-// once per block (the same expression and summation order in every block,
-// so the step is bit-identical to a separate alpha kernel), and every thread
-// issues the loads of all its rows before it waits for alpha, so the launch
-// is a couple of waves of long-lived blocks instead of many waves of blocks
-// that each wait on alpha's L2 round trips.  T = double: the FP64 CG (FP64
-// dots); T = float: the mixed form's inner CG (scaled FP32 dots).
+// z = D^-1 r, and the block's partials of r.z and ||r||^2; the subdomain's
+// last block to finish then ends the step (cg_step_finish, cg_step_arrive).
+// A block covers up to G consecutive tiles of one subdomain (d.ub_tile0 /
+// d.ub64_tile0; FP32: 8, FP64: 2, which keeps its registers, and so its
+// occupancy, up).  Every thread first issues the loads of all its rows; then
+// every warp forms alpha itself from the subdomain's p.q partials (the same
+// expression and summation order in every warp and block, so the step is
+// bit-identical to a separate alpha kernel, with no block-wide wait for
+// it).  Each thread adds its rows' r.z and r.r in row order, the block adds
+// its threads' sums in a fixed order and writes one partial pair per block.
+// T = double: the FP64 CG (FP64 dots, staged in shared memory: FP64 adds are
+// scarce); T = float: the mixed form's inner CG (scaled FP32 dots, FP32 warp
+// sums widened to FP64 across warps).
 template <class T, int G>
 __global__ void __launch_bounds__(kTileRows) k_cg_update_a(DevProblem d, CgVec<T> v, unsigned long long cond,
                                                            int use_cond) {
-  __shared__ double sm[G][2][kTileSlices];
-  __shared__ double sm64[sizeof(T) == 8 ? 2 * G : 1][sizeof(T) == 8 ? kTileRows : 1];
-  __shared__ T s_alpha;
+  __shared__ double sm[2][kTileSlices];
+  __shared__ double sm64[sizeof(T) == 8 ? 2 : 1][sizeof(T) == 8 ? kTileRows : 1];
   __shared__ bool s_last;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t t0 = (G == kUpdGroup ? d.ub_tile0 : d.ub64_tile0)[blockIdx.x];
+  const int64_t ub = blockIdx.x;
+  const int64_t t0 = (G == kUpdGroup ? d.ub_tile0 : d.ub64_tile0)[ub];
+  const int64_t* __restrict__ ub0 = G == kUpdGroup ? d.sub_ub0 : d.sub_ub64_0;
   const int s = d.tile_sub[t0];
   const int64_t ts0 = d.sub_tile0[s];
   if (!d.st.active[s]) {
@@ -338,18 +342,13 @@ __global__ void __launch_bounds__(kTileRows) k_cg_update_a(DevProblem d, CgVec<T
       di[j] = v.dinv[row];
     }
   }
-  if (warp == 0) {
-    const int64_t c0 = d.sub_part0[s];
-    const double pq = warp_sum_parts(d.part0, c0, d.sub_part0[s + 1] - c0);
-    if (lane == 0) s_alpha = (pq > 0.0 && isfinite(pq)) ? (T)(d.st.rho[s] / pq) : T(0);
-  }
-  __syncthreads();
-  const T alpha = s_alpha;
+  const int64_t c0 = d.sub_part0[s];
+  const double pq = warp_sum_parts(d.part0, c0, d.sub_part0[s + 1] - c0);
+  const T alpha = (pq > 0.0 && isfinite(pq)) ? (T)(d.st.rho[s] / pq) : T(0);
   const T sc = sizeof(T) == 4 ? (T)d.st.sc[s] : T(1);
-  const double isc2 = sizeof(T) == 4 ? d.st.isc2[s] : 1.0;
+  T a = T(0), b = T(0);
 #pragma unroll
   for (int j = 0; j < G; ++j) {
-    T a = T(0), b = T(0);
     if (j < nt) {
       const int64_t row = (t0 + j) * kTileRows + threadIdx.x;
       v.x[row] = fma(alpha, pr[j], xr[j]);
@@ -358,63 +357,50 @@ __global__ void __launch_bounds__(kTileRows) k_cg_update_a(DevProblem d, CgVec<T
       v.r[row] = r;
       v.z[row] = z;
       if constexpr (sizeof(T) == 8) {   // FP64: no scaling (FP64 multiplies are scarce)
-        a = r * z;
-        b = r * r;
+        a = fma(r, z, a);
+        b = fma(r, r, b);
       } else {
         const T rs = r * sc;
-        a = rs * (z * sc);
-        b = rs * rs;
-      }
-    }
-    if constexpr (sizeof(T) == 8) {
-      // staged in shared memory: about one FP64 add per value (block_sum_d)
-      sm64[2 * j][threadIdx.x] = a;
-      sm64[2 * j + 1][threadIdx.x] = b;
-    } else {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xffffffffu, a, o);
-        b += __shfl_xor_sync(0xffffffffu, b, o);
-      }
-      if (lane == 0) {
-        sm[j][0][warp] = (double)a * isc2;
-        sm[j][1][warp] = (double)b * isc2;
+        a = fma(rs, z * sc, a);
+        b = fma(rs, rs, b);
       }
     }
   }
-  __syncthreads();
   if constexpr (sizeof(T) == 8) {
-    // 8 threads per (tile, value) add interleaved eighths; then 8 partials each
-    double part = 0.0;
-    if (threadIdx.x < 16 * G) {
-      const int kv = threadIdx.x >> 3, c = threadIdx.x & 7;
-#pragma unroll 8
-      for (int i = 0; i < kTileRows / 8; ++i) part += sm64[kv][i * 8 + c];
+    double vv[2] = {a, b};
+    block_sum_d<2, kTileRows>(vv, sm64);
+    if (threadIdx.x == 0) {
+      d.part1[ub] = vv[0];
+      d.part2[ub] = vv[1];
+    }
+  } else {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+      const double isc2 = d.st.isc2[s];
+      sm[0][warp] = (double)a * isc2;
+      sm[1][warp] = (double)b * isc2;
     }
     __syncthreads();
-    if (threadIdx.x < 16 * G) sm64[threadIdx.x >> 3][threadIdx.x & 7] = part;
-    __syncthreads();
-    if (threadIdx.x < 2 * nt) {
-      double acc = 0.0;
+    if (threadIdx.x == 0) {
+      double s0 = 0.0, s1 = 0.0;
 #pragma unroll
-      for (int c = 0; c < 8; ++c) acc += sm64[threadIdx.x][c];
-      (threadIdx.x & 1 ? d.part2 : d.part1)[t0 + (threadIdx.x >> 1)] = acc;
-      __threadfence();   // each writer publishes its partial before the block's ticket
+      for (int w = 0; w < kTileSlices; ++w) {
+        s0 += sm[0][w];
+        s1 += sm[1][w];
+      }
+      d.part1[ub] = s0;
+      d.part2[ub] = s1;
     }
-  } else if (threadIdx.x < 2 * nt) {
-    const int j = threadIdx.x >> 1, which = threadIdx.x & 1;
-    double acc = 0.0;
-#pragma unroll
-    for (int w = 0; w < kTileSlices; ++w) acc += sm[j][which][w];
-    (which ? d.part2 : d.part1)[t0 + j] = acc;
-    __threadfence();   // each writer publishes its partial before the block's ticket
   }
   // the last block of the subdomain to get here finishes its CG step
   // (replaces a separate finaliser launch per step)
-  __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned nblk = (unsigned)((d.sub_tile0[s + 1] - ts0 + G - 1) / G);
+    __threadfence();   // publish the partials before the ticket
+    const unsigned nblk = (unsigned)(ub0[s + 1] - ub0[s]);
     const unsigned t = atomicAdd(&d.st.ucnt[s], 1u);
     s_last = t == nblk - 1u;
     if (s_last) d.st.ucnt[s] = 0u;
@@ -422,7 +408,7 @@ __global__ void __launch_bounds__(kTileRows) k_cg_update_a(DevProblem d, CgVec<T
   __syncthreads();
   if (!s_last || warp != 0) return;
   __threadfence();
-  cg_step_finish(d, s, lane);
+  cg_step_finish(d, ub0, s, lane);
   if (lane == 0) cg_step_arrive(d, cond, use_cond);
 }
 

@@ -523,43 +523,63 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
   return std::string();
 }
 
-void build_box_layout(HostProblem& hp) {
+void box_cta_tables(HostProblem& hp, int zchunk) {
+  const int ns = hp.nsub;
+  hp.box_cta_sub.clear();
+  hp.box_sub_cta0.assign(ns + 1, 0);
+  int64_t ctas = 0;
+  for (int s = 0; s < ns; ++s) {
+    int32_t* dm = &hp.box_dims[kBoxDims * (size_t)s];
+    const int bnx = dm[0], bny = dm[1], bnz = dm[2];
+    const int ncb = (int)(((int64_t)bnx * bny + kTileRows - 1) / kTileRows);
+    const int nch = std::max(1, (bnz + zchunk - 1) / zchunk);
+    const int zc = (bnz + nch - 1) / nch;          // chunks of nearly equal length
+    const int nch_used = (bnz + zc - 1) / zc;
+    dm[4] = zc;
+    dm[5] = ncb;
+    dm[6] = nch_used;
+    hp.box_sub_cta0[s] = ctas;
+    for (int64_t c = 0; c < (int64_t)ncb * nch_used; ++c) hp.box_cta_sub.push_back(s);
+    ctas += (int64_t)ncb * nch_used;
+  }
+  hp.box_sub_cta0[ns] = ctas;
+  hp.box_ctas = ctas;
+}
+
+void build_box_layout(HostProblem& hp, int zchunk) {
   const int ns = hp.nsub;
   hp.box_voff.assign(ns, 0);
-  hp.box_dims.assign(4 * (size_t)ns, 0);
+  hp.box_dims.assign(kBoxDims * (size_t)ns, 0);
   hp.box_tile_sub.clear();
   hp.box_sub_tile0.assign(ns + 1, 0);
   hp.box_ub_tile0.clear();
-  hp.box_cta_sub.clear();
-  hp.box_sub_cta0.assign(ns + 1, 0);
+  hp.box_sub_ub0.assign(ns + 1, 0);
   hp.box_max_nx = 0;
-  int64_t rows = 0, tiles = 0, ctas = 0;
+  int64_t rows = 0, tiles = 0;
   for (int s = 0; s < ns; ++s) {
     const SubInfo& S = hp.sub[s];
     const int bnx = S.i1 - S.i0 + 1, bny = S.j1 - S.j0 + 1, bnz = S.k1 - S.k0 + 1;
-    hp.box_dims[4 * s + 0] = bnx;
-    hp.box_dims[4 * s + 1] = bny;
-    hp.box_dims[4 * s + 2] = bnz;
-    hp.box_dims[4 * s + 3] = S.fmask;
+    int32_t* dm = &hp.box_dims[kBoxDims * (size_t)s];
+    dm[0] = bnx;
+    dm[1] = bny;
+    dm[2] = bnz;
+    dm[3] = S.fmask;
     hp.box_max_nx = std::max(hp.box_max_nx, bnx);
     const int64_t nb = (int64_t)bnx * bny * bnz;
     const int64_t nt = std::max<int64_t>(1, (nb + kTileRows - 1) / kTileRows);
     hp.box_voff[s] = rows;
     hp.box_sub_tile0[s] = tiles;
     for (int64_t t = 0; t < nt; ++t) hp.box_tile_sub.push_back(s);
+    hp.box_sub_ub0[s] = (int64_t)hp.box_ub_tile0.size();
     for (int64_t t = 0; t < nt; t += kUpdGroup) hp.box_ub_tile0.push_back(tiles + t);
     rows += nt * kTileRows;
     tiles += nt;
-    const int64_t nc = ((int64_t)bnx * bny + kTileRows - 1) / kTileRows;
-    hp.box_sub_cta0[s] = ctas;
-    for (int64_t c = 0; c < nc; ++c) hp.box_cta_sub.push_back(s);
-    ctas += nc;
   }
   hp.box_sub_tile0[ns] = tiles;
-  hp.box_sub_cta0[ns] = ctas;
+  hp.box_sub_ub0[ns] = (int64_t)hp.box_ub_tile0.size();
   hp.box_rows = rows;
   hp.box_tiles = tiles;
-  hp.box_ctas = ctas;
+  box_cta_tables(hp, zchunk);
   hp.row_box.assign(hp.vec_rows, -1);
   for (int64_t r = 0; r < hp.vec_rows; ++r) {
     const int32_t b = hp.row_boxidx[r];

@@ -37,6 +37,7 @@ constexpr int kTxPlane = kTileRows + 6 * kTensorMaxNx;   // staged input plane: 
 constexpr int kTxRows = kTileRows + 2 * kTensorMaxNx;    // y-pass outputs: the CTA's rows, all x
 constexpr int kTxPre = (kTxPlane + kTileRows - 1) / kTileRows;
 constexpr int kTxY = (kTxRows + kTileRows - 1) / kTileRows;
+constexpr int kTxMaxRows = kTileRows / 3 + 2;   // rows 256 columns can touch (boxes are >= 3 nodes wide)
 
 // FP32 bands of every subdomain: the mass as it is, the stiffness with the
 // transmission term p of each interface side added at that side's end node
@@ -44,7 +45,7 @@ constexpr int kTxY = (kTxRows + kTileRows - 1) / kTileRows;
 // +y, +z sides -- and p_hi on its -x, -y, -z sides).  One block per subdomain.
 __global__ void k_tensor_coef(DevProblem d) {
   const int s = blockIdx.x;
-  const int* dims = d.box_dims + 4 * s;
+  const int* dims = d.box_dims + kBoxDims * s;
   const int nx = dims[0], ny = dims[1], nz = dims[2], fm = dims[3];
   const double* c = d.tc + 4 * s;
   const int64_t b0 = (int64_t)d.box_band0[s] * 5;
@@ -69,20 +70,27 @@ __global__ void k_tensor_coef(DevProblem d) {
 // k_cg_spmv_dir32): t = A z, then p = z + beta p, q = t + beta q (first step
 // beta = 0: p = z, q = t) and the CTA's partial of p.q (scaled FP32 dots as in
 // the SELL kernel) into part0[cta].  MODE 1: y = A x (x, y in the box layout).
+// A CTA covers 256 (x, y) columns of one box and one chunk of its z range
+// (box_dims: the chunk length and the number of column blocks), marching
+// over the chunk's planes and the two halo planes on either side.  Every
+// global load a plane needs is issued one plane ahead.
 template <int MODE>
-__global__ void __launch_bounds__(kTileRows) k_tensor32(DevProblem d, const float* __restrict__ xin,
-                                                        float* __restrict__ yout) {
+__global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const float* __restrict__ xin,
+                                                           float* __restrict__ yout) {
   __shared__ float S[2][kTxPlane];
   __shared__ float TM[kTxRows], TK[kTxRows];
+  __shared__ float CY[kTxMaxRows][10];   // y bands of the CTA's rows: M then K~
   __shared__ double red[kTileSlices];
   const int cta = blockIdx.x;
   const int s = d.cta_sub[cta];
   if (MODE == 0 && !d.st.active[s]) return;
-  const int* dims = d.box_dims + 4 * s;
-  const int nx = dims[0], ny = dims[1], nz = dims[2], fm = dims[3];
+  const int* dims = d.box_dims + kBoxDims * s;
+  const int nx = dims[0], ny = dims[1], nz = dims[2], fm = dims[3], zc = dims[4], ncb = dims[5];
   const int nxy = nx * ny;
   const int64_t voff = d.box_voff[s];
-  const int c0 = (int)(cta - d.sub_cta0[s]) * kTileRows;
+  const int local = (int)(cta - d.sub_cta0[s]);
+  const int c0 = (local % ncb) * kTileRows;
+  const int k0 = (local / ncb) * zc, k1 = min(nz, k0 + zc);   // output planes [k0, k1)
   const int col = c0 + (int)threadIdx.x;
   const bool valid = col < nxy;
   const int jlo = c0 / nx, jhi = min(ny - 1, (c0 + kTileRows - 1) / nx);
@@ -91,6 +99,10 @@ __global__ void __launch_bounds__(kTileRows) k_tensor32(DevProblem d, const floa
   const int64_t bx = (int64_t)d.box_band0[s] * 5, by = bx + 5 * (int64_t)nx, bz = by + 5 * (int64_t)ny;
   const float* __restrict__ cK = d.cK32;
   const float* __restrict__ cM = d.cM32;
+  for (int t = threadIdx.x; t < 5 * nrow; t += kTileRows) {
+    CY[t / 5][t % 5] = cM[by + 5 * (int64_t)jlo + t];
+    CY[t / 5][5 + t % 5] = cK[by + 5 * (int64_t)jlo + t];
+  }
   float kx[5], mx[5];
 #pragma unroll
   for (int a = 0; a < 5; ++a) {
@@ -133,32 +145,46 @@ __global__ void __launch_bounds__(kTileRows) k_tensor32(DevProblem d, const floa
     beta = (float)b64;
     sc = d.st.sc[s];
   }
+  // epilogue operands of an output plane, fetched one plane ahead
+  float zb[5], kb[5], pold = 0.f, qold = 0.f;
+  auto fetch_out = [&](int k) {
+    if (k < k0 || k >= k1) return;
+    const int64_t cz = bz + 5 * (int64_t)k;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) { zb[c] = cM[cz + c]; kb[c] = cK[cz + c]; }
+    if (MODE == 0 && valid && !first) {
+      const int64_t row = voff + col + (int64_t)nxy * k;
+      pold = d.p32[row];
+      qold = d.q32[row];
+    }
+  };
   float ph[5], qh[5], zh[5];
 #pragma unroll
-  for (int c = 0; c < 5; ++c) { ph[c] = 0.f; qh[c] = 0.f; zh[c] = 0.f; }
+  for (int c = 0; c < 5; ++c) { ph[c] = 0.f; qh[c] = 0.f; zh[c] = 0.f; zb[c] = 0.f; kb[c] = 0.f; }
   float vv = 0.f;
-  fetch(-2);
+  fetch(k0 - 2);
+  fetch_out(k0);
   int buf = 0;
-  for (int kk = -2; kk < nz + 2; ++kk) {
+  for (int kk = k0 - 2; kk < k1 + 2; ++kk) {
 #pragma unroll
     for (int m = 0; m < kTxPre; ++m) {
       const int idx = (int)threadIdx.x + m * kTileRows;
       if (idx < nload) S[buf][idx] = pre[m];
     }
     __syncthreads();
-    if (kk + 1 < nz + 2) fetch(kk + 1);   // the next plane's loads overlap this plane's work
-    // y pass: My z and Ky z on the CTA's rows, every x
+    if (kk + 1 < k1 + 2) fetch(kk + 1);   // the next plane's loads overlap this plane's work
+    // y pass: My z and K~y z on the CTA's rows, every x
 #pragma unroll
     for (int m = 0; m < kTxY; ++m) {
       if (yrow[m] >= 0) {
         const int idx = (int)threadIdx.x + m * kTileRows;
-        const int64_t cy = by + 5 * (int64_t)(jlo + yrow[m]);
+        const float* cy = CY[yrow[m]];
         float sm = 0.f, sk = 0.f;
 #pragma unroll
         for (int b = 0; b < 5; ++b) {
           const float v = S[buf][idx + b * nx];
-          sm = fmaf(cM[cy + b], v, sm);
-          sk = fmaf(cK[cy + b], v, sk);
+          sm = fmaf(cy[b], v, sm);
+          sk = fmaf(cy[5 + b], v, sk);
         }
         TM[idx] = sm;
         TK[idx] = sk;
@@ -166,7 +192,7 @@ __global__ void __launch_bounds__(kTileRows) k_tensor32(DevProblem d, const floa
     }
     __syncthreads();
     // x pass for this thread's column: P = K~x (My z) + Mx (K~y z), Q = Mx (My z)
-    float P = 0.f, Q = 0.f, zc = 0.f;
+    float P = 0.f, Q = 0.f, zc_own = 0.f;
     if (valid) {
       const int base = (j - jlo) * nx + i;
 #pragma unroll
@@ -178,33 +204,39 @@ __global__ void __launch_bounds__(kTileRows) k_tensor32(DevProblem d, const floa
           Q = fmaf(mx[a], tm, Q);
         }
       }
-      zc = S[buf][base + 2 * nx];
+      zc_own = S[buf][base + 2 * nx];
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) { ph[c] = ph[c + 1]; qh[c] = qh[c + 1]; zh[c] = zh[c + 1]; }
     ph[4] = P;
     qh[4] = Q;
-    zh[4] = zc;
+    zh[4] = zc_own;
     const int k = kk - 2;   // output plane: its neighbours k-2 .. k+2 are in the rings
-    if (valid && k >= 0) {
-      const int64_t cz = bz + 5 * (int64_t)k;
-      float t = 0.f;
+    if (k >= k0) {
+      float zb_k[5], kb_k[5];
 #pragma unroll
-      for (int c = 0; c < 5; ++c) t = fmaf(cM[cz + c], ph[c], fmaf(cK[cz + c], qh[c], t));
-      if (dcol || ((fm & 16) && k == 0) || ((fm & 32) && k == nz - 1)) t = 0.f;
-      const int64_t row = voff + col + (int64_t)nxy * k;
-      if (MODE == 0) {
-        const float z = zh[2];
-        float p = z, q = t;
-        if (!first) {
-          p = fmaf(beta, d.p32[row], z);
-          q = fmaf(beta, d.q32[row], t);
+      for (int c = 0; c < 5; ++c) { zb_k[c] = zb[c]; kb_k[c] = kb[c]; }
+      const float p_old = pold, q_old = qold;
+      fetch_out(k + 1);
+      if (valid) {
+        float t = 0.f;
+#pragma unroll
+        for (int c = 0; c < 5; ++c) t = fmaf(zb_k[c], ph[c], fmaf(kb_k[c], qh[c], t));
+        if (dcol || ((fm & 16) && k == 0) || ((fm & 32) && k == nz - 1)) t = 0.f;
+        const int64_t row = voff + col + (int64_t)nxy * k;
+        if (MODE == 0) {
+          const float z = zh[2];
+          float p = z, q = t;
+          if (!first) {
+            p = fmaf(beta, p_old, z);
+            q = fmaf(beta, q_old, t);
+          }
+          d.p32[row] = p;
+          d.q32[row] = q;
+          vv = fmaf(p * sc, q * sc, vv);
+        } else {
+          yout[row] = t;
         }
-        d.p32[row] = p;
-        d.q32[row] = q;
-        vv = fmaf(p * sc, q * sc, vv);
-      } else {
-        yout[row] = t;
       }
     }
     buf ^= 1;
@@ -233,6 +265,7 @@ DevProblem fp32_view(const DevProblem& d) {
   v.sub_tile0 = d.box_sub_tile0;
   v.n_tiles = d.box_n_tiles;
   v.ub_tile0 = d.box_ub_tile0;
+  v.sub_ub0 = d.box_sub_ub0;
   v.n_ublocks = d.box_n_ublocks;
   v.sub_part0 = d.sub_cta0;
   return v;
