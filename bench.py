@@ -2,9 +2,16 @@
 
 One step = one full Schwarz solve (Robin RHS, batched subdomain Jacobi-PCG,
 Robin exchange, global residual -- every step of the hot path) from u = 0
-to a relative residual of 1e-8 on the 64^3 layered workload (unit cube, Q2,
-4 x 4 x 4 subdomains, 2,048,383 unknowns).  The subdomain matrices (1.6 GB
-of SELL data) are larger than L2, so no flush is needed between steps.
+to a relative residual of 1e-8 on the regional workload: a 100 x 100 x 30
+box, Q2 on 128 x 128 x 48 elements graded in z, 192 subdomains of uneven
+size from jittered cuts (6,177,375 unknowns), Gaussian-random-field density
+plus a basin.  The headline is the mixed form (FP32 subdomain CG inside FP64
+refinement); the FP64 form (the paper's setting) and the FP64 refinement
+form are sub-lines with their own, stated step counts (each solve takes
+10-60 s).  The subdomain matrices and vectors (about 9 GB) are larger than
+L2, so no flush is needed between steps.  Every line states the relative L2
+error of its solution against the FP64 oracle's monolithic solve (PCG to
+1e-13), computed on the host cores while the GPU is timed.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -29,15 +36,21 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "DOF/s solved to 1e-8 rel residual, mixed vs FP64; SpMV GB/s vs HBM peak"
-WORKLOAD = "layered64"
+WORKLOAD = "regional"
 P_ROBIN = 20.0
-# Robin parameter per workload (layered64: best of the batched sampling and
-# the tolerance sweeps; others scaled by the same search)
-P_FOR = {"layered64": 20.0, "regional": 1.0, "layered160": 40.0, "layered48": 10.0}
+# Robin parameter per workload, chosen by the batched evaluation of sampled p
+# (Sec. 4; osm_sample_p race mode, fewest Schwarz iterations).  regional: 16
+# log-uniform p in [0.8, 3] (SplitMix64 seed 0), mixed form, winner 1.6664
+# at 660 iterations; layered64: 20 from the sweeps of the 64^3 workload.
+P_FOR = {"layered64": 20.0, "regional": 1.6664, "layered160": 40.0, "layered48": 10.0}
 RTOL = 1e-8
 INNER_RTOL = 1e-10
 MIXED_INNER_RTOL = 0.4
 FALLBACK_HBM = 6800.0
+SUB_WARMUP, SUB_STEPS = 1, 2     # the FP64 and FP64-refinement sub-lines
+E2E_STEPS = 5                    # end-to-end solves through the public API (headline)
+ORACLE_TOL = 1e-13               # the oracle's monolithic PCG
+ORACLE_WAIT_S = 1500.0           # longest wait for the oracle after the GPU work
 
 
 def _is_slab(name):
@@ -252,15 +265,22 @@ def _cpu_baseline(prob, p, n_outer_needed, name=WORKLOAD, budget_s=20.0):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (the paper's method in plain C on
+    the host cores) on the bench workload.  Each step is one of its Schwarz
+    iterations (subdomain PCG to 1e-10, Sec. 6, OpenMP over subdomains);
+    DOF/s = unknowns / (mean step time x the oracle's own iteration count to
+    1e-8, tests/golden/<workload>_iterations.json)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     import gen
-    prob = gen.workload(WORKLOAD)
-    n_outer = _reference_iterations()
+    name = args.workload or WORKLOAD
+    prob = gen.workload(name)
+    p_robin = P_FOR.get(name, P_ROBIN)
+    n_outer = _reference_iterations(name)
     threads = int(os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1)))
     import oracle
-    S = oracle.Schwarz.from_problem(prob, p=P_ROBIN)
+    S = oracle.Schwarz.from_problem(prob, p=p_robin)
     for _ in range(args.warmup):
         S.iterate(inner_rtol=INNER_RTOL)
     times = []
@@ -270,12 +290,13 @@ def run_reference(args):
         times.append(time.perf_counter() - t)
     per_iter = sum(times) / len(times)
     value = prob.n_dofs / (per_iter * n_outer)
-    sample = (f"each step: one Schwarz iteration of the FP64 oracle on {WORKLOAD} (OpenMP over "
-              f"subdomains); DOF/s = unknowns / (mean step time x {n_outer} iterations to {RTOL:g})")
+    sample = (f"each step: one Schwarz iteration of the FP64 oracle on {name} (OpenMP over subdomains, after "
+              f"{args.warmup} warm-up iterations); DOF/s = unknowns / (mean step time x {n_outer} oracle "
+              f"iterations to {RTOL:g})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "DOF/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_iter * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": _workload_desc(prob, P_ROBIN)},
+            "data": "synthetic", "config": {"workload": _workload_desc(prob, p_robin, name)},
             "cpu_baseline": {"value": value, "unit": "DOF/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "DOF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -283,8 +304,10 @@ def run_reference(args):
     return 0
 
 
-def _reference_iterations():
-    path = os.path.join(ROOT, "tests", "golden", "layered64_iterations.json")
+def _reference_iterations(name=WORKLOAD):
+    """The FP64 oracle's Schwarz iteration count to 1e-8 on a workload, from
+    the committed record written by tests/golden/make_iterations.py."""
+    path = os.path.join(ROOT, "tests", "golden", f"{name}_iterations.json")
     try:
         with open(path) as f:
             return int(json.load(f)["schwarz_iterations"])
@@ -292,14 +315,15 @@ def _reference_iterations():
         return 150
 
 
-def _measure(sol, prob, args, ws, local, barrier, use_graph_note, rtol=RTOL):
-    """Warm-up, the timed region (CUDA events, clocks sampled) and the
-    end-to-end run through the public API from host buffers."""
+def _measure(sol, prob, warmup, steps, e2e_steps, ws, local, barrier, use_graph_note, rtol=RTOL):
+    """Warm-up, the timed region (CUDA events, clocks sampled) and, if
+    e2e_steps > 0, the end-to-end run through the public API from host
+    buffers."""
     import numpy as np
     import torch
     stream = torch.cuda.current_stream()
     phi = torch.zeros(sol.info["n_nodes"], dtype=torch.float64, device="cuda")
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         sol.solve(rtol, phi=phi)
     st = sol.stats()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -309,44 +333,112 @@ def _measure(sol, prob, args, ws, local, barrier, use_graph_note, rtol=RTOL):
         barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             _, it, rel = sol.solve(rtol, phi=phi)
             launches += sol.stats()["n_launches"]
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = ev0.elapsed_time(ev1) / steps
     value, ms_max = aggregate_over_ranks(ms, prob.n_dofs, device="cuda")
-    # end to end through the public API: every step copies the density from
-    # pinned host memory to the device, assembles the load there
-    # (osm_set_density_dev), solves, and copies the solution back to pinned
-    # host memory
-    phi_host = torch.empty(sol.info["n_nodes"], dtype=torch.float64, pin_memory=True)
-    drho_host = torch.from_numpy(np.ascontiguousarray(prob.drho, dtype=np.float64)).pin_memory()
-    drho_dev = torch.empty(drho_host.shape, dtype=torch.float64, device="cuda")
-    drho_dev.copy_(drho_host)
-    sol.set_density_dev(drho_dev)        # first call allocates the device assembly data
-    barrier()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        drho_dev.copy_(drho_host, non_blocking=True)
-        sol.set_density_dev(drho_dev)
-        sol.solve(rtol, phi=phi)
-        phi_host.copy_(phi, non_blocking=True)
-        torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    e2e_value, _ = aggregate_over_ranks(e2e_s * 1e3, prob.n_dofs, device="cuda")
-    return {
-        "value": value, "ms_per_step": ms_max, "relres": rel,
+    out = {
+        "value": value, "ms_per_step": ms_max, "steps": steps, "warmup": max(warmup, 1), "relres": rel,
         "schwarz_iterations": st["n_outer"], "cg_steps_per_solve": st["n_cg_steps"],
         "launches_per_step": int(st["n_launches"]), "gpu_launches": int(launches),
         "clocks": clk.summary(), "launch_mode": use_graph_note,
-        "e2e": {"value": e2e_value, "unit": "DOF/s",
-                "h2d_bytes_per_step": int(drho_host.numel()) * 8,     # the density, one FP64 per element
-                "d2h_bytes_per_step": sol.info["n_nodes"] * 8},       # phi
-        "_phi": phi,
+        "_phi": phi.cpu().numpy(),
     }
+    if e2e_steps > 0:
+        # end to end through the public API: every step copies the density
+        # from pinned host memory to the device, assembles the load there
+        # (osm_set_density_dev), solves, and copies the solution back to
+        # pinned host memory
+        phi_host = torch.empty(sol.info["n_nodes"], dtype=torch.float64, pin_memory=True)
+        drho_host = torch.from_numpy(np.ascontiguousarray(prob.drho, dtype=np.float64)).pin_memory()
+        drho_dev = torch.empty(drho_host.shape, dtype=torch.float64, device="cuda")
+        drho_dev.copy_(drho_host)
+        sol.set_density_dev(drho_dev)        # first call allocates the device assembly data
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            drho_dev.copy_(drho_host, non_blocking=True)
+            sol.set_density_dev(drho_dev)
+            sol.solve(rtol, phi=phi)
+            phi_host.copy_(phi, non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e_value, _ = aggregate_over_ranks(e2e_s * 1e3, prob.n_dofs, device="cuda")
+        out["e2e"] = {"value": e2e_value, "unit": "DOF/s", "steps": e2e_steps,
+                      "h2d_bytes_per_step": int(drho_host.numel()) * 8,     # the density, one FP64 per element
+                      "d2h_bytes_per_step": sol.info["n_nodes"] * 8}        # phi
+    return out
+
+
+def _oracle_job(name, path, threads):
+    """The oracle's monolithic FP64 solve of a workload (Jacobi-PCG to
+    ORACLE_TOL), run in a spawned process on the host cores while the GPU
+    is timed; writes the full-grid solution (.npy) and its record (.json)."""
+    os.environ["OMP_NUM_THREADS"] = str(threads)
+    import numpy as np
+
+    import gen
+    import oracle
+    t0 = time.perf_counter()
+    prob = gen.workload(name)
+    G = oracle.GlobalSystem(prob.xc, prob.yc, prob.zc, prob.drho)
+    t_asm = time.perf_counter() - t0
+    x, it, rel = G.solve(tol=ORACLE_TOL)
+    np.save(path, G.to_grid(x))
+    with open(path + ".json", "w") as f:
+        json.dump({"pcg_iterations": int(it), "relres": float(rel), "assembly_s": round(t_asm, 1),
+                   "seconds": round(time.perf_counter() - t0, 1), "threads": threads}, f)
+
+
+class OracleSolution:
+    """The oracle's solution of the bench workload, computed concurrently."""
+
+    def __init__(self, name):
+        import multiprocessing as mp
+        self.dir = tempfile.mkdtemp(prefix="osm_oracle_")
+        self.path = os.path.join(self.dir, "phi.npy")
+        cores = os.cpu_count() or 1
+        self.threads = max(1, cores - 2)        # leave the bench's host thread and the clock sampler a core
+        self.t0 = time.perf_counter()
+        self.proc = mp.get_context("spawn").Process(target=_oracle_job, args=(name, self.path, self.threads),
+                                                    daemon=True)
+        self.proc.start()
+        self.phi = None
+        self.record = None
+
+    def wait(self, limit_s):
+        self.proc.join(timeout=max(1.0, limit_s - (time.perf_counter() - self.t0)))
+        if self.proc.is_alive():
+            self.proc.terminate()
+            self.proc.join(timeout=10)
+            self.record = {"error": f"oracle solve not finished within {limit_s:.0f} s"}
+            return False
+        try:
+            import numpy as np
+            self.phi = np.load(self.path)
+            with open(self.path + ".json") as f:
+                self.record = json.load(f)
+        except Exception as e:          # the child failed
+            self.record = {"error": f"oracle solve failed: {e!r} (exit code {self.proc.exitcode})"}
+            return False
+        return True
+
+    def rel_l2(self, phi):
+        import numpy as np
+        if self.phi is None:
+            return None
+        return float(np.linalg.norm(phi - self.phi) / np.linalg.norm(self.phi))
+
+    def close(self):
+        import shutil
+        if self.proc.is_alive():
+            self.proc.terminate()
+        shutil.rmtree(self.dir, ignore_errors=True)
 
 
 FP64_FMA_PEAK_GFLOPS = 1256.0   # measured FP64 FMA throughput (profiles/peaks.md)
@@ -377,11 +469,40 @@ def _roofline(sol, prec, name):
             "col_bytes": sol.info["col_bytes_fp64" if prec in (0, 3) else "col_bytes_fp32"]}
 
 
+def _spmv_roofline_sell32(sol):
+    """The FP32 SELL CG-step SpMV (k_cg_spmv_dir32) from the autotuner's
+    timing of its fastest variant (CUDA events, timed alone, every subdomain
+    active): the metric's 'SpMV GB/s' on this workload, also when the solve
+    itself runs the tensor-product operator."""
+    i = sol.info
+    ms_all = [m for m in list(i["spmv_ms_fp32"]) + list(i["spmv_ms16_fp32"]) if m > 0]
+    if not ms_all:
+        return None
+    ms = min(ms_all)
+    k = (list(i["spmv_ms_fp32"]) + list(i["spmv_ms16_fp32"])).index(ms)
+    cb = 2 if k >= 2 else 4
+    nbytes = i["nnz"] * (4 + cb) + i["n_slices"] * 8 + i["n_local"] * 8 + 12 * i["n_local"]
+    peak, kind = _peaks()
+    achieved = nbytes / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "kernel": "k_cg_spmv_dir32 (batched SELL-32 FP32 SpMV of the CG "
+            "step + direction epilogue, fastest variant, every subdomain active)",
+            "peak_kind": f"{kind} hbm_gbs (copy), burst (kernel timed alone)", "ms_per_launch": round(ms, 5),
+            "algorithmic_bytes": nbytes, "col_bytes": cb, "source": "autotuner timing at setup"}
+
+
 def run_ours(args):
     import torch
 
     import gen
     ws, rank, local = _dist()
+    name = args.workload or WORKLOAD
+    single = name not in ("batch64", "sample32", "grad48")
+    # the oracle's monolithic solve runs on the host cores while the GPU is
+    # timed (a spawned process: no CUDA state is inherited)
+    orc = None
+    if single and rank == 0 and ws == 1 and not args.no_oracle and not _is_slab(name):
+        orc = OracleSolution(name)
     torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
@@ -398,7 +519,6 @@ def run_ours(args):
         if ws > 1:
             torch.distributed.barrier()
 
-    name = args.workload or WORKLOAD
     if name == "batch64":
         return run_batch(args, pkg, ws, rank, local, barrier)
     if name == "sample32":
@@ -413,14 +533,33 @@ def run_ours(args):
     note = "one CUDA graph per solve" if use_graph else "host-driven launches (profiling mode)"
     res = {}
     sols = {}
-    for prec in (["mixed", "fp64", "fp64_refine"] if args.prec == "both" else [args.prec]):
+    precs = ["mixed", "fp64", "fp64_refine"] if args.prec == "both" else [args.prec]
+    head = precs[0]
+    for prec in precs:
         sol = pkg.Solver.from_problem(prob, p=p_robin, tc=tc[0] if tc else None, inner_rtol=INNER_RTOL,
                                       max_outer=5000, prec=prec, mixed_inner_rtol=MIXED_INNER_RTOL,
                                       use_graph=use_graph)
-        sols[prec] = sol
-        res[prec] = _measure(sol, prob, args, ws, local, barrier, note, rtol)
-        res[prec]["setup_s"] = round(sol.info["setup_seconds"], 2)
-    head = "mixed" if "mixed" in res else "fp64"
+        if prec == head:
+            r = _measure(sol, prob, args.warmup, args.steps, min(args.steps, E2E_STEPS), ws, local, barrier, note,
+                         rtol)
+        else:
+            r = _measure(sol, prob, SUB_WARMUP, SUB_STEPS, 0, ws, local, barrier, note, rtol)
+        r["setup_s"] = round(sol.info["setup_seconds"], 2)
+        res[prec] = r
+        if prec == "mixed":
+            r["fp32_operator"] = {1: "SELL-32 matrix", 2: "tensor-product (matrix-free)"}.get(sol.info["fp32_operator"])
+            r["roofline_dominant"] = (_roofline(sol, 2, "k_tensor32 (tensor-product FP32 operator of the CG step + "
+                                                       "direction epilogue, every subdomain active)")
+                                      if sol.info["fp32_operator"] == 2 else
+                                      _roofline(sol, 2, "k_cg_spmv_dir32 (batched SELL-32 FP32 SpMV of the CG step "
+                                                       "+ direction epilogue, every subdomain active)"))
+            r["spmv_roofline"] = _spmv_roofline_sell32(sol)
+        else:
+            r["roofline_dominant"] = _roofline(sol, 3, "k_cg_spmv<double> (batched SELL-32 FP64 SpMV of the CG "
+                                                       "step, every subdomain active)")
+            r["roofline_alu"] = _roofline_alu(sol, r["roofline_dominant"]["ms_per_launch"])
+        del sol
+        torch.cuda.empty_cache()
     h = res[head]
     line = {"metric": METRIC, "value": h["value"], "unit": "DOF/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": h["ms_per_step"], "higher_is_better": True,
@@ -428,43 +567,50 @@ def run_ours(args):
             "dtype": "f32 inner CG + f64 refinement" if head == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": _workload_desc(prob, p_robin, name, tc),
-                       "precision": (f"mixed: FP32 subdomain CG to {MIXED_INNER_RTOL:g} of the FP64 defect, "
-                                     "FP64 defect, exchange and stop test" if head == "mixed" else "FP64"),
-                       "l2": "inputs larger than L2 (1.6 GB of subdomain matrices), no flush",
+                       "precision": (f"mixed: FP32 subdomain CG to {MIXED_INNER_RTOL:g} of the FP64 defect "
+                                     f"({h.get('fp32_operator')} operator), FP64 defect, exchange and stop test"
+                                     if head == "mixed" else "FP64"),
+                       "l2": "inputs larger than L2 (several GB of subdomain matrices and vectors), no flush",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                        "launch": h["launch_mode"]},
             "gpu_launches": h["gpu_launches"], "schwarz_iterations": h["schwarz_iterations"],
             "cg_steps_per_solve": h["cg_steps_per_solve"], "relres": h["relres"],
-            "setup_s": h["setup_s"], "e2e": h["e2e"], "clocks": h["clocks"]}
-    if head == "mixed":
-        line["roofline"] = _roofline(sols["mixed"], 2, "k_cg_spmv_dir32 (batched SELL-32 FP32 SpMV of the CG step "
-                                                        "+ direction epilogue, every subdomain active)")
-    else:
-        line["roofline"] = _roofline(sols["fp64"], 3, "k_cg_spmv<double> (batched SELL-32 FP64 SpMV of the CG step, "
-                                                       "every subdomain active)")
-    keys = ("value", "ms_per_step", "schwarz_iterations", "cg_steps_per_solve", "relres", "gpu_launches", "e2e",
-            "clocks", "setup_s")
+            "setup_s": h["setup_s"], "e2e": h["e2e"], "clocks": h["clocks"],
+            "roofline": h["roofline_dominant"]}
+    if "spmv_roofline" in h:
+        line["spmv_roofline"] = h["spmv_roofline"]
+    keys = ("value", "ms_per_step", "steps", "warmup", "schwarz_iterations", "cg_steps_per_solve", "relres",
+            "gpu_launches", "clocks", "setup_s")
     if "fp64" in res and head != "fp64":
         f = res["fp64"]
-        # the mixed solution against the FP64 GPU solution of the same problem (both to rtol)
-        import torch
-        d = torch.linalg.norm(h["_phi"] - f["_phi"]) / torch.linalg.norm(f["_phi"])
-        line["mixed_vs_fp64_rel_l2"] = float(d)
         line["fp64"] = {k: f[k] for k in keys}
         line["fp64"]["precision"] = f"FP64, subdomain PCG to {INNER_RTOL:g} of ||b_i|| every iteration (Sec. 6)"
-        line["fp64"]["roofline"] = _roofline(sols["fp64"], 3, "k_cg_spmv<double> (batched SELL-32 FP64 SpMV of the "
-                                                               "CG step, every subdomain active)")
-        line["fp64"]["roofline_alu"] = _roofline_alu(sols["fp64"], line["fp64"]["roofline"]["ms_per_launch"])
+        line["fp64"]["roofline"] = f["roofline_dominant"]
+        line["fp64"]["roofline_alu"] = f["roofline_alu"]
         line["mixed_speedup_vs_fp64"] = round(h["value"] / f["value"], 3)
+        line["mixed_vs_fp64_rel_l2"] = float(
+            __import__("numpy").linalg.norm(h["_phi"] - f["_phi"]) / __import__("numpy").linalg.norm(f["_phi"]))
     if "fp64_refine" in res:
         f = res["fp64_refine"]
         line["fp64_refine"] = {k: f[k] for k in keys}
         line["fp64_refine"]["precision"] = (f"FP64, the mixed form's algorithm: subdomain CG to "
                                             f"{MIXED_INNER_RTOL:g} of each iteration's defect")
+        line["fp64_refine"]["roofline"] = f["roofline_dominant"]
         if head == "mixed":
             line["mixed_speedup_vs_fp64_refine"] = round(h["value"] / f["value"], 3)
+    # error of every result against the FP64 oracle's monolithic solve
+    if orc is not None:
+        ok = orc.wait(ORACLE_WAIT_S)
+        line["oracle"] = {"solve": f"monolithic Jacobi-PCG to {ORACLE_TOL:g} relative residual, FP64, "
+                                   f"{orc.threads} host threads", **(orc.record or {})}
+        for prec, r in res.items():
+            err = orc.rel_l2(r["_phi"]) if ok else None
+            tgt = line if prec == head else line.get(prec)
+            if tgt is not None:
+                tgt["rel_l2_vs_oracle"] = err
+        orc.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and not _is_slab(name):
-        n_outer = res["fp64"]["schwarz_iterations"] if "fp64" in res else _reference_iterations()
+        n_outer = res["fp64"]["schwarz_iterations"] if "fp64" in res else _reference_iterations(name)
         line["cpu_baseline"] = _cpu_baseline(prob, p_robin, n_outer, name)
     if _is_slab(name):
         line["cpu_baseline"] = None   # one oracle Schwarz iteration of a 19.5M-node slab run takes far too long
@@ -678,6 +824,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle", action="store_true",
+                    help="skip the oracle's monolithic solve (the error of each line against it)")
     ap.add_argument("--prec", choices=("both", "mixed", "fp64"), default="both")
     ap.add_argument("--workload", default=None,
                     help="another workload: layered48, regional, layered160, slab32/64/128, batch64 "
