@@ -222,6 +222,15 @@ osm_status upload_problem(osm_ctx* h) {
   d.fm_col = fm_col; d.fm_val = fm_val; d.face_s = face_s; d.face_t = face_t; d.face_n = face_n;
   d.face_eo = face_eo;
   OSM_CUDA(h, dalloc(h, &d.lam, 2 * (size_t)hp.n_fent));
+  // interface-column layer of K_i (stop test)
+  d.n_lrow = (int32_t)hp.li_row.size();
+  int32_t *li_row, *li_ptr, *li_col;
+  double* li_val;
+  OSM_CUDA(h, upload(h, &li_row, hp.li_row));
+  OSM_CUDA(h, upload(h, &li_ptr, hp.li_ptr));
+  OSM_CUDA(h, upload(h, &li_col, hp.li_col));
+  OSM_CUDA(h, upload(h, &li_val, hp.li_val));
+  d.li_row = li_row; d.li_ptr = li_ptr; d.li_col = li_col; d.li_val = li_val;
   // copies, outputs, stop test
   d.n_nodes = hp.n_nodes;
   int32_t *cp_ptr, *cp_idx, *can2vec;
@@ -659,51 +668,69 @@ osm_status build_lsolve_graph(osm_ctx* h) {
   return OSM_OK;
 }
 
+// Adds a conditional WHILE node after the work captured so far on cs (whose
+// capture target is `graph`) and makes it the capture's only dependency.
+cudaError_t add_while_after_capture(cudaStream_t cs, cudaGraph_t graph, cudaGraphConditionalHandle c,
+                                    cudaGraphNodeParams* p, cudaGraphNode_t* node) {
+  cudaStreamCaptureStatus cst;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+  if (e != cudaSuccess) return e;
+  *p = cudaGraphNodeParams{};
+  p->type = cudaGraphNodeTypeConditional;
+  p->conditional.handle = c;
+  p->conditional.type = cudaGraphCondTypeWhile;
+  p->conditional.size = 1;
+  e = cudaGraphAddNode(node, graph, deps, nullptr, ndeps, p);
+  if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, node, nullptr, 1, cudaStreamSetCaptureDependencies);
+  return e;
+}
+
+// The solve graph:
+//   RHS gather, CG start                                  (first iteration)
+//   while (running) {                                      // Schwarz iteration
+//     CG finaliser; while (any subdomain active) CG step   // subdomain solves
+//     [u += e]; Robin exchange                             // Sec. 3
+//     RHS gather, CG start of the next iteration (r = b - A u, y = A u)
+//     stop test on y: K ubar = y - T u + K (ubar - u)      // Sec. 6
+//   }
+// The next iteration's CG start comes before the stop test so that its
+// product A u serves the stop test too: one SpMV over the FP64 matrices per
+// Schwarz iteration instead of two.
 osm_status build_graph(osm_ctx* h) {
   if (h->exec) return OSM_OK;
   cudaStream_t cs = h->cap_stream;
   cudaGraph_t g = nullptr;
   OSM_CUDA(h, cudaGraphCreate(&g, 0));
   h->graph = g;
-  cudaGraphConditionalHandle c_out, c_in;
-  OSM_CUDA(h, cudaGraphConditionalHandleCreate(&c_out, g, 1, cudaGraphCondAssignDefault));
-  cudaGraphNodeParams po{};
-  po.type = cudaGraphNodeTypeConditional;
-  po.conditional.handle = c_out;
-  po.conditional.type = cudaGraphCondTypeWhile;
-  po.conditional.size = 1;
-  cudaGraphNode_t n_out;
-  OSM_CUDA(h, cudaGraphAddNode(&n_out, g, nullptr, nullptr, 0, &po));
-  cudaGraph_t body = po.conditional.phGraph_out[0];
-  OSM_CUDA(h, cudaGraphConditionalHandleCreate(&c_in, body, 0, 0));
-  // outer body: RHS, CG start, [inner loop], exchange, stop test
-  OSM_CUDA(h, cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   const bool mixed = h->opts.prec == OSM_MIXED;
   const int refine = h->opts.prec == OSM_FP64_REFINE;
+  cudaGraphConditionalHandle c_out, c_in;
+  OSM_CUDA(h, cudaGraphConditionalHandleCreate(&c_out, g, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams po{}, pi{};
+  cudaGraphNode_t n_out = nullptr, n_in = nullptr;
+  cudaGraph_t captured = nullptr;
+  // first iteration's RHS and CG start, then the outer loop
+  OSM_CUDA(h, cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = launch_rhs_gather(h->d, cs);
-  if (e == cudaSuccess)
-    e = mixed ? launch_cg_init_mixed(h->d, cs, c_in, 1) : launch_cg_init(h->d, cs, c_in, 1, refine);
-  cudaGraphNodeParams pi{};
-  cudaGraphNode_t n_in = nullptr;
-  if (e == cudaSuccess) {
-    cudaStreamCaptureStatus cst;
-    const cudaGraphNode_t* deps = nullptr;
-    size_t ndeps = 0;
-    e = cudaStreamGetCaptureInfo(cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
-    if (e == cudaSuccess) {
-      pi.type = cudaGraphNodeTypeConditional;
-      pi.conditional.handle = c_in;
-      pi.conditional.type = cudaGraphCondTypeWhile;
-      pi.conditional.size = 1;
-      e = cudaGraphAddNode(&n_in, body, deps, nullptr, ndeps, &pi);
-    }
-    if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cs, &n_in, nullptr, 1, cudaStreamSetCaptureDependencies);
-  }
+  if (e == cudaSuccess) e = launch_cg_start(h->d, cs, mixed);
+  if (e == cudaSuccess) e = add_while_after_capture(cs, g, c_out, &po, &n_out);
+  cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+  OSM_CUDA(h, e);
+  OSM_CUDA(h, e2);
+  cudaGraph_t body = po.conditional.phGraph_out[0];
+  OSM_CUDA(h, cudaGraphConditionalHandleCreate(&c_in, body, 0, 0));
+  // outer body
+  OSM_CUDA(h, cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+  e = launch_fin_init(h->d, cs, c_in, 1, mixed ? 1 : refine);
+  if (e == cudaSuccess) e = add_while_after_capture(cs, body, c_in, &pi, &n_in);
   if (e == cudaSuccess && mixed) e = launch_mixed_correct(h->d, cs);
   if (e == cudaSuccess) e = launch_exchange(h->d, cs);
-  if (e == cudaSuccess) e = launch_residual(h->d, cs, c_out, 1);
-  cudaGraph_t captured = nullptr;
-  cudaError_t e2 = cudaStreamEndCapture(cs, &captured);
+  if (e == cudaSuccess) e = launch_rhs_gather(h->d, cs);
+  if (e == cudaSuccess) e = launch_cg_start(h->d, cs, mixed);
+  if (e == cudaSuccess) e = launch_stop_test(h->d, cs, c_out, 1);
+  e2 = cudaStreamEndCapture(cs, &captured);
   OSM_CUDA(h, e);
   OSM_CUDA(h, e2);
   // inner body: one CG iteration on every active subdomain
@@ -745,11 +772,12 @@ osm_status run_iterations(osm_ctx* h, double rtol, int max_outer) {
     if (st != OSM_OK) return st;
     OSM_CUDA(h, cudaGraphLaunch(h->exec, h->stream));
   } else {
+    // the same launch sequence as the graph (build_graph), driven from the host
+    const bool mixed = h->opts.prec == OSM_MIXED;
+    OSM_CUDA(h, launch_rhs_gather(h->d, h->stream));
+    OSM_CUDA(h, launch_cg_start(h->d, h->stream, mixed));
     for (int n = 0; n < max_outer; ++n) {
-      const bool mixed = h->opts.prec == OSM_MIXED;
-      OSM_CUDA(h, launch_rhs_gather(h->d, h->stream));
-      OSM_CUDA(h, mixed ? launch_cg_init_mixed(h->d, h->stream, 0, 0)
-                        : launch_cg_init(h->d, h->stream, 0, 0, h->opts.prec == OSM_FP64_REFINE));
+      OSM_CUDA(h, launch_fin_init(h->d, h->stream, 0, 0, mixed ? 1 : h->opts.prec == OSM_FP64_REFINE));
       for (int it = 0; it <= h->opts.max_inner; ++it) {
         OSM_CUDA(h, cudaMemcpyAsync(h->ctl_host, h->d.ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, h->stream));
         OSM_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -758,7 +786,9 @@ osm_status run_iterations(osm_ctx* h, double rtol, int max_outer) {
       }
       if (mixed) OSM_CUDA(h, launch_mixed_correct(h->d, h->stream));
       OSM_CUDA(h, launch_exchange(h->d, h->stream));
-      OSM_CUDA(h, launch_residual(h->d, h->stream, 0, 0));
+      OSM_CUDA(h, launch_rhs_gather(h->d, h->stream));
+      OSM_CUDA(h, launch_cg_start(h->d, h->stream, mixed));
+      OSM_CUDA(h, launch_stop_test(h->d, h->stream, 0, 0));
       OSM_CUDA(h, cudaMemcpyAsync(h->ctl_host, h->d.ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, h->stream));
       OSM_CUDA(h, cudaStreamSynchronize(h->stream));
       if (h->ctl_host->running == 0 || h->ctl_host->stop) break;
@@ -915,10 +945,13 @@ osm_status osm_setup(const osm_mesh* mesh, const double* drho, const osm_decomp*
   if (st != OSM_OK) return st;
   OSM_CUDA(h, cudaStreamSynchronize(h->stream));
   h->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  // host copies of the large arrays are not needed any more
+  // host copies of the large arrays are not needed any more (the layer's row
+  // list stays: its length counts launches)
   std::vector<int32_t>().swap(h->hp.cols);
   std::vector<double>().swap(h->hp.vals);
   std::vector<float>().swap(h->hp.vals32);
+  std::vector<int32_t>().swap(h->hp.li_col);
+  std::vector<double>().swap(h->hp.li_val);
   return OSM_OK;
 }
 
@@ -1071,6 +1104,8 @@ osm_status osm_setup_batch(int32_t n_inst, const osm_mesh* meshes, const double*
   std::vector<int32_t>().swap(h->hp.cols);
   std::vector<double>().swap(h->hp.vals);
   std::vector<float>().swap(h->hp.vals32);
+  std::vector<int32_t>().swap(h->hp.li_col);
+  std::vector<double>().swap(h->hp.li_val);
   return OSM_OK;
 }
 
@@ -1195,13 +1230,15 @@ osm_status osm_stats(osm_handle h, osm_stats_t* o) {
     const int64_t per_outer = 3 + mixed + faces + 3;
     o->n_launches = 1 + per_outer * c.n_outer + 5 * (int64_t)c.total_inner;
   } else {
-    // solve: per Schwarz iteration RHS gather, CG start, its finaliser, FP64
-    // correction (mixed), exchange (if any face), average, K ubar, face
-    // correction (if any interface), residual partials, residual finaliser;
-    // per CG step SpMV (+ direction epilogue in FP32) and update (+ the
-    // step's finish), plus the FP64 direction; plus the nodal load once
-    const int64_t per_outer = 3 + mixed + faces + 2 + (h->hp.irow.empty() ? 0 : 1) + 2;
-    o->n_launches = 1 + per_outer * c.n_outer + (mixed ? 2 : 3) * (int64_t)c.total_inner;
+    // solve: once the nodal load, the first RHS gather and CG start; per
+    // Schwarz iteration the CG finaliser, FP64 correction (mixed), exchange
+    // (if any face), the next RHS gather and CG start, average, face
+    // correction (if any interface), interface layer (if any), residual
+    // partials, residual finaliser; per CG step SpMV (+ direction epilogue in
+    // FP32) and update (+ the step's finish), plus the FP64 direction
+    const int64_t per_outer = 1 + mixed + faces + 2 + 1 + (h->hp.irow.empty() ? 0 : 1) +
+                              (h->hp.li_row.empty() ? 0 : 1) + 2;
+    o->n_launches = 3 + per_outer * c.n_outer + (mixed ? 2 : 3) * (int64_t)c.total_inner;
   }
   o->relres = c.relres;
   o->status = c.status;

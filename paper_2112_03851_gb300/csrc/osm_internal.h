@@ -129,6 +129,14 @@ struct HostProblem {
   int64_t box_rows = 0, box_tiles = 0, box_ctas = 0;
   int32_t box_max_nx = 0;
 
+  // Interface-column layer of the Neumann matrices: for every row of K_i
+  // with entries in columns that are interface rows of the same subdomain,
+  // those entries (CSR over the rows li_row, ascending).  The stop test forms
+  // K_i ubar_i = A_i u_i - T_i u_i + K_i (ubar_i - u_i), and ubar_i - u_i
+  // vanishes off the interface rows.
+  std::vector<int32_t> li_row, li_ptr, li_col;
+  std::vector<double> li_val;
+
   // Copies of each node of the full grid (vector rows, subdomain order).
   std::vector<int32_t> cp_ptr;        // n_nodes + 1
   std::vector<int32_t> cp_idx;
@@ -253,6 +261,10 @@ struct DevProblem {
   const int32_t *face_s, *face_t, *face_n;
   const int64_t* face_eo;
   double* lam;
+  // interface-column layer of K_i (HostProblem li_*)
+  int32_t n_lrow;
+  const int32_t *li_row, *li_ptr, *li_col;
+  const double* li_val;
   // copies
   int64_t n_nodes;
   const int32_t *cp_ptr, *cp_idx;
@@ -407,6 +419,14 @@ cudaError_t launch_mp_cg_iteration(const DevProblem& d, const DevSample& m, cuda
 cudaError_t launch_mp_exchange_residual(const DevProblem& d, const DevSample& m, cudaStream_t s,
                                         unsigned long long cond, int use_cond, int mixed);
 cudaError_t launch_residual(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
+// CG start of the next Schwarz iteration (the SpMV kernel only: r = b - A u
+// or the FP64 defect, y = A u kept for the stop test) and its finaliser.
+cudaError_t launch_cg_start(const DevProblem& d, cudaStream_t s, int mixed);
+cudaError_t launch_fin_init(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond,
+                            int defect_norm);
+// Stop test after launch_cg_start: ubar, K ubar = y - T u + K (ubar - u), the
+// relative residual, the outer loop condition.
+cudaError_t launch_stop_test(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
 cudaError_t launch_apply(const DevProblem& d, int op, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_gather_local(const DevProblem& d, const double* vec, double* canon, cudaStream_t s);
 cudaError_t launch_spmv_plain(const DevProblem& d, const double* x, double* y, cudaStream_t s);

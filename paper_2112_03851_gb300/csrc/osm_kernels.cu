@@ -68,7 +68,8 @@ __global__ void k_rhs_gather(DevProblem d) {
 }
 
 // CG start from the warm iterate x: r = b - A x, z = D^-1 r, p = z, and the
-// tile partials of ||r||^2, ||b||^2 and r.z (finalised by k_fin_init).
+// tile partials of ||r||^2, ||b||^2 and r.z (finalised by k_fin_init); y =
+// A x is kept for the stop test of the iteration that produced x.
 template <int RPL, bool C16>
 __global__ void __launch_bounds__(kTileRows) k_cg_init(DevProblem d) {
   __shared__ double sm[3][kTileRows / RPL];
@@ -84,6 +85,7 @@ __global__ void __launch_bounds__(kTileRows) k_cg_init(DevProblem d) {
     const double b = d.b[row[k]];
     const double r = b - ax[k];
     const double z = d.dinv[row[k]] * r;
+    d.y[row[k]] = ax[k];
     d.r[row[k]] = r;
     d.z[row[k]] = z;
     d.p[row[k]] = z;
@@ -426,7 +428,8 @@ __global__ void k_profile_state(DevProblem d) {
 // Mixed precision, start of one refinement step: FP64 defect
 // d = b - A u (FP64 values and accumulation), then the FP32 CG on A e = d
 // from e = 0: r = d, z = D^-1 r, p = z, and the tile partials of ||d||^2,
-// ||b||^2 and r.z (k_fin_init decides which subdomains are corrected).
+// ||b||^2 and r.z (k_fin_init decides which subdomains are corrected); y =
+// A u is kept for the stop test.
 template <int RPL, bool C16>
 __global__ void __launch_bounds__(kTileRows) k_cg_init_mixed(DevProblem d) {
   __shared__ double sm[3][kTileRows / RPL];
@@ -441,6 +444,7 @@ __global__ void __launch_bounds__(kTileRows) k_cg_init_mixed(DevProblem d) {
   for (int k = 0; k < RPL; ++k) {
     const double b = d.b[row[k]];
     const double dfc = b - ax[k];
+    d.y[row[k]] = ax[k];
     const float r = (float)dfc;
     float z = 0.f;
     // the FP32 solve's row: the same row, or its row in the tensor form's box layout
@@ -589,6 +593,20 @@ __global__ void k_face_correct(DevProblem d, const double* __restrict__ x, doubl
   for (int32_t e = d.im_ptr[k]; e < d.im_ptr[k + 1]; ++e) acc = fma(d.im_t[e], x[d.im_col[e]], acc);
   const int32_t row = d.irow[k];
   y[row] -= acc;
+}
+
+// Stop test: y = A u (from the CG start) becomes K ubar = A u - T u +
+// K (ubar - u); ubar - u vanishes off the interface rows, so only the
+// interface-column layer of K is applied (w = ubar on every copy, x = u).
+__global__ void k_stop_layer(DevProblem d) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= d.n_lrow) return;
+  double acc = 0.0;
+  for (int32_t e = d.li_ptr[k]; e < d.li_ptr[k + 1]; ++e) {
+    const int32_t c = d.li_col[e];
+    acc = fma(d.li_val[e], d.w[c] - d.x[c], acc);
+  }
+  d.y[d.li_row[k]] += acc;
 }
 
 // Stop test, step 2: r = sum_copies f - sum_copies K_i ubar per node, and
@@ -821,6 +839,27 @@ cudaError_t launch_residual(const DevProblem& d, cudaStream_t s, unsigned long l
   k_average<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
   OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_spmv_plain, s, d, d.w, d.y);
   if (d.n_irow) k_face_correct<<<blocks_for(d.n_irow, 256), 256, 0, s>>>(d, d.w, d.y);
+  k_residual<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
+  k_residual_fin<<<1, kResFinThreads, 0, s>>>(d, cond, use_cond);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_start(const DevProblem& d, cudaStream_t s, int mixed) {
+  if (mixed) OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_cg_init_mixed, s, d);
+  else OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_cg_init, s, d);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fin_init(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond,
+                            int defect_norm) {
+  k_fin_init<<<fin_blocks(d), kTileRows, 0, s>>>(d, defect_norm, cond, use_cond);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stop_test(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
+  k_average<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
+  if (d.n_irow) k_face_correct<<<blocks_for(d.n_irow, 256), 256, 0, s>>>(d, d.x, d.y);
+  if (d.n_lrow) k_stop_layer<<<blocks_for(d.n_lrow, 256), 256, 0, s>>>(d);
   k_residual<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
   k_residual_fin<<<1, kResFinThreads, 0, s>>>(d, cond, use_cond);
   return cudaGetLastError();

@@ -277,6 +277,14 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
     std::vector<int64_t> pos, pos32;
   };
   std::vector<std::vector<IfaceRow>> irows(nsub);
+  // interface-column layer of K_i: (row, column, K value) of every entry whose
+  // column is an interface row of the same subdomain (the stop test's K ubar)
+  struct LayerRow {
+    int32_t row;
+    std::vector<int32_t> col;
+    std::vector<double> kv;
+  };
+  std::vector<std::vector<LayerRow>> lrows(nsub);
   std::vector<int64_t> nnz_sub(nsub, 0);
 #pragma omp parallel for schedule(dynamic)
   for (int s = 0; s < nsub; ++s) {
@@ -296,6 +304,8 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
                          S.iface[2] && j == S.j0, S.iface[3] && j == S.j1,
                          S.iface[4] && k == S.k0, S.iface[5] && k == S.k1};
       bool is_if = on_face[0] || on_face[1] || on_face[2] || on_face[3] || on_face[4] || on_face[5];
+      LayerRow lr;
+      lr.row = (int32_t)(S.voff + r);
       IfaceRow ir;
       if (is_if) {
         ir.row = (int32_t)(S.voff + r);
@@ -317,6 +327,11 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
             int64_t vpos = off + (int64_t)(jn / 2) * 64 + lane * 2 + (jn % 2);
             hp.cols[cpos] = col;
             hp.vals[vpos] = v;
+            if ((S.iface[0] && ii == S.i0) || (S.iface[1] && ii == S.i1) || (S.iface[2] && jj == S.j0) ||
+                (S.iface[3] && jj == S.j1) || (S.iface[4] && kk == S.k0) || (S.iface[5] && kk == S.k1)) {
+              lr.col.push_back((int32_t)(S.voff + col));
+              lr.kv.push_back(v);
+            }
             if (want_fp32) hp.vals32[cpos] = (float)v;
             if (col == r) hp.kdiag[S.voff + r] = v;
             if (is_if) {
@@ -371,6 +386,7 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
       nnz += jn;
       hp.dinv0[S.voff + r] = 1.0 / hp.kdiag[S.voff + r];
       if (is_if) irows[s].push_back(std::move(ir));
+      if (!lr.col.empty()) lrows[s].push_back(std::move(lr));
     }
     // padding rows of partially filled slices point at themselves
     for (int32_t r = S.n; r < S.npad; ++r) {
@@ -517,6 +533,21 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
   }
   if (hp.ilam.size() != lam_rows.size()) return "internal error: interface rows and face entries disagree";
 
+  // ---- interface-column layer, rows in ascending order
+  hp.li_row.clear(); hp.li_col.clear(); hp.li_val.clear();
+  hp.li_ptr.assign(1, 0);
+  for (int s = 0; s < nsub; ++s) {
+    auto& rows = lrows[s];
+    std::sort(rows.begin(), rows.end(), [](const LayerRow& x, const LayerRow& y) { return x.row < y.row; });
+    for (const LayerRow& lr : rows) {
+      hp.li_row.push_back(lr.row);
+      hp.li_col.insert(hp.li_col.end(), lr.col.begin(), lr.col.end());
+      hp.li_val.insert(hp.li_val.end(), lr.kv.begin(), lr.kv.end());
+      if ((int64_t)hp.li_col.size() >= ((int64_t)1 << 31)) return "interface layer too large for 32-bit offsets";
+      hp.li_ptr.push_back((int32_t)hp.li_col.size());
+    }
+  }
+
   // ---- load
   build_load(hp, drho, hp.f);
   single_instance_tables(hp);
@@ -637,6 +668,7 @@ std::string merge_problems(std::vector<HostProblem>& parts, HostProblem& out) {
   o.im_ptr.push_back(0);
   o.fm_ptr.push_back(0);
   o.cp_ptr.push_back(0);
+  o.li_ptr.push_back(0);
   for (int i = 0; i < o.n_inst; ++i) {
     HostProblem& p = parts[i];
     const int32_t sub_off = o.nsub;
@@ -691,6 +723,12 @@ std::string merge_problems(std::vector<HostProblem>& parts, HostProblem& out) {
     append(o.fm_val, p.fm_val);
     append(o.fs_val, p.fs_val);
     for (size_t k = 1; k < p.cp_ptr.size(); ++k) o.cp_ptr.push_back((int32_t)(p.cp_ptr[k] + cp_off));
+    const int64_t li_off = (int64_t)o.li_col.size();
+    if (li_off + (int64_t)p.li_col.size() >= ((int64_t)1 << 31)) return "batched interface layer too large";
+    append_shift(o.li_row, p.li_row, (int32_t)vec_off);
+    append_shift(o.li_col, p.li_col, (int32_t)vec_off);
+    append(o.li_val, p.li_val);
+    for (size_t k = 1; k < p.li_ptr.size(); ++k) o.li_ptr.push_back((int32_t)(p.li_ptr[k] + li_off));
     append_shift(o.cp_idx, p.cp_idx, (int32_t)vec_off);
     for (int s = 0; s < p.nsub; ++s) o.sub_inst.push_back(i);
     add_rblocks(o, i, node_off, node_off + p.n_nodes);

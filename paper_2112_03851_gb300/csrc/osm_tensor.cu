@@ -38,6 +38,7 @@ constexpr int kTxRows = kTileRows + 2 * kTensorMaxNx;    // y-pass outputs: the 
 constexpr int kTxPre = (kTxPlane + kTileRows - 1) / kTileRows;
 constexpr int kTxY = (kTxRows + kTileRows - 1) / kTileRows;
 constexpr int kTxMaxRows = kTileRows / 3 + 2;   // rows 256 columns can touch (boxes are >= 3 nodes wide)
+constexpr int kTxStages = 4;                     // input planes in flight
 
 // FP32 bands of every subdomain: the mass as it is, the stiffness with the
 // transmission term p of each interface side added at that side's end node
@@ -66,18 +67,33 @@ __global__ void k_tensor_coef(DevProblem d) {
   }
 }
 
+// Asynchronous 4-byte global -> shared copy (LDGSTS); src_bytes = 0 fills
+// the destination with zero (halo rows outside the box).
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // MODE 0: one step of the FP32 inner CG (the tensor counterpart of
 // k_cg_spmv_dir32): t = A z, then p = z + beta p, q = t + beta q (first step
 // beta = 0: p = z, q = t) and the CTA's partial of p.q (scaled FP32 dots as in
 // the SELL kernel) into part0[cta].  MODE 1: y = A x (x, y in the box layout).
 // A CTA covers 256 (x, y) columns of one box and one chunk of its z range
 // (box_dims: the chunk length and the number of column blocks), marching
-// over the chunk's planes and the two halo planes on either side.  Every
-// global load a plane needs is issued one plane ahead.
+// over the chunk's planes and the two halo planes on either side.  The input
+// planes stream through kTxStages shared-memory stages filled by
+// asynchronous copies issued kTxStages - 1 planes ahead, together with the
+// old p and q of the output plane they complete; the z bands are loaded one
+// plane ahead.
 template <int MODE>
 __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const float* __restrict__ xin,
                                                            float* __restrict__ yout) {
-  __shared__ float S[2][kTxPlane];
+  __shared__ __align__(16) float S[kTxStages][kTxPlane];
+  __shared__ float PQ[MODE == 0 ? kTxStages : 1][2][MODE == 0 ? kTileRows : 1];   // old p, q of an output plane
   __shared__ float TM[kTxRows], TK[kTxRows];
   __shared__ float CY[kTxMaxRows][10];   // y bands of the CTA's rows: M then K~
   __shared__ double red[kTileSlices];
@@ -112,15 +128,16 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
   // column on the outer boundary (x or y side): its rows are Dirichlet
   const bool dcol = ((fm & 1) && i == 0) || ((fm & 2) && i == nx - 1) || ((fm & 4) && j == 0) ||
                     ((fm & 8) && j == ny - 1);
-  // plane-relative offsets of this thread's staged values (the same in every plane)
+  // plane-relative offsets of this thread's staged values (the same in every
+  // plane); -1: a halo row outside the box, staged as zero
   int goff[kTxPre];
 #pragma unroll
   for (int m = 0; m < kTxPre; ++m) {
     const int idx = (int)threadIdx.x + m * kTileRows;
-    goff[m] = -1;
+    goff[m] = -2;   // beyond the staged region: no copy
     if (idx < nload) {
       const int r = idx / nx, jj = jlo - 2 + r;
-      if (jj >= 0 && jj < ny) goff[m] = (idx - r * nx) + nx * jj;
+      goff[m] = (jj >= 0 && jj < ny) ? (idx - r * nx) + nx * jj : -1;
     }
   }
   int yrow[kTxY];
@@ -130,13 +147,6 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
     yrow[m] = idx < ntr ? idx / nx : -1;
   }
   const float* __restrict__ src = MODE == 0 ? d.z32 : xin;
-  float pre[kTxPre];
-  auto fetch = [&](int kk) {
-    const bool in = kk >= 0 && kk < nz;
-    const int64_t pl = voff + (int64_t)nxy * kk;
-#pragma unroll
-    for (int m = 0; m < kTxPre; ++m) pre[m] = (in && goff[m] >= 0) ? src[pl + goff[m]] : 0.f;
-  };
   float beta = 0.f, sc = 1.f;
   bool first = true;
   if (MODE == 0) {
@@ -145,55 +155,71 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
     beta = (float)b64;
     sc = d.st.sc[s];
   }
-  // epilogue operands of an output plane, fetched one plane ahead
-  float zb[5], kb[5], pold = 0.f, qold = 0.f;
+  // copies into stage st of input plane kk and (CG step) of the old p, q of
+  // output plane kk - 2, which is produced when plane kk is consumed; one
+  // commit group per plane, empty outside the box, so that the group count
+  // stays uniform
+  auto issue = [&](int kk, int st) {
+    if (kk >= 0 && kk < nz) {
+      const float* pl = src + voff + (int64_t)nxy * kk;
+#pragma unroll
+      for (int m = 0; m < kTxPre; ++m)
+        if (goff[m] >= -1) cp_async4(&S[st][threadIdx.x + m * kTileRows], pl + max(goff[m], 0), goff[m] >= 0);
+    }
+    if (MODE == 0 && !first && valid && kk - 2 >= k0 && kk - 2 < k1) {
+      const int64_t row = voff + col + (int64_t)nxy * (kk - 2);
+      cp_async4(&PQ[st][0][threadIdx.x], d.p32 + row, true);
+      cp_async4(&PQ[st][1][threadIdx.x], d.q32 + row, true);
+    }
+    cp_async_commit();
+  };
+  // z bands of an output plane, fetched one plane ahead
+  float zb[5], kb[5];
   auto fetch_out = [&](int k) {
     if (k < k0 || k >= k1) return;
     const int64_t cz = bz + 5 * (int64_t)k;
 #pragma unroll
     for (int c = 0; c < 5; ++c) { zb[c] = cM[cz + c]; kb[c] = cK[cz + c]; }
-    if (MODE == 0 && valid && !first) {
-      const int64_t row = voff + col + (int64_t)nxy * k;
-      pold = d.p32[row];
-      qold = d.q32[row];
-    }
   };
   float ph[5], qh[5], zh[5];
 #pragma unroll
   for (int c = 0; c < 5; ++c) { ph[c] = 0.f; qh[c] = 0.f; zh[c] = 0.f; zb[c] = 0.f; kb[c] = 0.f; }
   float vv = 0.f;
-  fetch(k0 - 2);
+#pragma unroll
+  for (int st = 0; st < kTxStages - 1; ++st) issue(k0 - 2 + st, st);
   fetch_out(k0);
-  int buf = 0;
+  int st = 0;
   for (int kk = k0 - 2; kk < k1 + 2; ++kk) {
+    // plane kk + stages - 1 into the stage freed at the end of the last plane
+    issue(kk + kTxStages - 1, st == 0 ? kTxStages - 1 : st - 1);
+    cp_async_wait<kTxStages - 1>();   // this thread's copies of plane kk have landed
+    __syncthreads();                  // ... and every other thread's
+    const bool pin = kk >= 0 && kk < nz;
+    float zc_own = 0.f;
+    if (pin) {
+      // y pass: My z and K~y z on the CTA's rows, every x
 #pragma unroll
-    for (int m = 0; m < kTxPre; ++m) {
-      const int idx = (int)threadIdx.x + m * kTileRows;
-      if (idx < nload) S[buf][idx] = pre[m];
-    }
-    __syncthreads();
-    if (kk + 1 < k1 + 2) fetch(kk + 1);   // the next plane's loads overlap this plane's work
-    // y pass: My z and K~y z on the CTA's rows, every x
+      for (int m = 0; m < kTxY; ++m) {
+        if (yrow[m] >= 0) {
+          const int idx = (int)threadIdx.x + m * kTileRows;
+          const float* cy = CY[yrow[m]];
+          float sm = 0.f, sk = 0.f;
 #pragma unroll
-    for (int m = 0; m < kTxY; ++m) {
-      if (yrow[m] >= 0) {
-        const int idx = (int)threadIdx.x + m * kTileRows;
-        const float* cy = CY[yrow[m]];
-        float sm = 0.f, sk = 0.f;
-#pragma unroll
-        for (int b = 0; b < 5; ++b) {
-          const float v = S[buf][idx + b * nx];
-          sm = fmaf(cy[b], v, sm);
-          sk = fmaf(cy[5 + b], v, sk);
+          for (int b = 0; b < 5; ++b) {
+            const float v = S[st][idx + b * nx];
+            sm = fmaf(cy[b], v, sm);
+            sk = fmaf(cy[5 + b], v, sk);
+          }
+          TM[idx] = sm;
+          TK[idx] = sk;
         }
-        TM[idx] = sm;
-        TK[idx] = sk;
       }
+      if (valid) zc_own = S[st][(j - jlo + 2) * nx + i];
     }
-    __syncthreads();
+    __syncthreads();   // TM, TK complete; stage st is free for the next issue
     // x pass for this thread's column: P = K~x (My z) + Mx (K~y z), Q = Mx (My z)
-    float P = 0.f, Q = 0.f, zc_own = 0.f;
-    if (valid) {
+    float P = 0.f, Q = 0.f;
+    if (pin && valid) {
       const int base = (j - jlo) * nx + i;
 #pragma unroll
       for (int a = 0; a < 5; ++a) {
@@ -204,7 +230,6 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
           Q = fmaf(mx[a], tm, Q);
         }
       }
-      zc_own = S[buf][base + 2 * nx];
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) { ph[c] = ph[c + 1]; qh[c] = qh[c + 1]; zh[c] = zh[c + 1]; }
@@ -216,7 +241,6 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
       float zb_k[5], kb_k[5];
 #pragma unroll
       for (int c = 0; c < 5; ++c) { zb_k[c] = zb[c]; kb_k[c] = kb[c]; }
-      const float p_old = pold, q_old = qold;
       fetch_out(k + 1);
       if (valid) {
         float t = 0.f;
@@ -227,9 +251,9 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
         if (MODE == 0) {
           const float z = zh[2];
           float p = z, q = t;
-          if (!first) {
-            p = fmaf(beta, p_old, z);
-            q = fmaf(beta, q_old, t);
+          if (!first) {   // this thread's own staged values: no barrier needed
+            p = fmaf(beta, PQ[st][0][threadIdx.x], z);
+            q = fmaf(beta, PQ[st][1][threadIdx.x], t);
           }
           d.p32[row] = p;
           d.q32[row] = q;
@@ -239,8 +263,9 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
         }
       }
     }
-    buf ^= 1;
+    st = st + 1 == kTxStages ? 0 : st + 1;
   }
+  cp_async_wait<0>();   // no copy outlives the CTA
   if (MODE == 0) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
