@@ -532,12 +532,21 @@ def run_ours(args):
     use_graph = 0 if args.launch == "host" else 1
     note = "one CUDA graph per solve" if use_graph else "host-driven launches (profiling mode)"
     res = {}
-    sols = {}
     precs = ["mixed", "fp64", "fp64_refine"] if args.prec == "both" else [args.prec]
     head = precs[0]
+    # the mixed form's inner tolerance, tuned on this workload and GPU (cached)
+    tin, tune_rec = MIXED_INNER_RTOL, None
+    if "mixed" in precs and not args.no_tune:
+        from paper_2112_03851_gb300 import tune
+
+        def make(t):
+            return pkg.Solver.from_problem(prob, p=p_robin, tc=tc[0] if tc else None, inner_rtol=INNER_RTOL,
+                                           max_outer=5000, prec="mixed", mixed_inner_rtol=t, use_graph=use_graph)
+        tin, tune_rec = tune.tune_inner_rtol(make, tune.problem_key(prob, p_robin, rtol), rtol=rtol)
+        torch.cuda.empty_cache()
     for prec in precs:
         sol = pkg.Solver.from_problem(prob, p=p_robin, tc=tc[0] if tc else None, inner_rtol=INNER_RTOL,
-                                      max_outer=5000, prec=prec, mixed_inner_rtol=MIXED_INNER_RTOL,
+                                      max_outer=5000, prec=prec, mixed_inner_rtol=tin,
                                       use_graph=use_graph)
         if prec == head:
             r = _measure(sol, prob, args.warmup, args.steps, min(args.steps, E2E_STEPS), ws, local, barrier, note,
@@ -567,7 +576,7 @@ def run_ours(args):
             "dtype": "f32 inner CG + f64 refinement" if head == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": _workload_desc(prob, p_robin, name, tc),
-                       "precision": (f"mixed: FP32 subdomain CG to {MIXED_INNER_RTOL:g} of the FP64 defect "
+                       "precision": (f"mixed: FP32 subdomain CG to {tin:g} of the FP64 defect "
                                      f"({h.get('fp32_operator')} operator), FP64 defect, exchange and stop test"
                                      if head == "mixed" else "FP64"),
                        "l2": "inputs larger than L2 (several GB of subdomain matrices and vectors), no flush",
@@ -579,6 +588,8 @@ def run_ours(args):
             "roofline": h["roofline_dominant"]}
     if "spmv_roofline" in h:
         line["spmv_roofline"] = h["spmv_roofline"]
+    if tune_rec is not None:
+        line["inner_rtol_tuning"] = tune_rec
     keys = ("value", "ms_per_step", "steps", "warmup", "schwarz_iterations", "cg_steps_per_solve", "relres",
             "gpu_launches", "clocks", "setup_s")
     if "fp64" in res and head != "fp64":
@@ -594,7 +605,7 @@ def run_ours(args):
         f = res["fp64_refine"]
         line["fp64_refine"] = {k: f[k] for k in keys}
         line["fp64_refine"]["precision"] = (f"FP64, the mixed form's algorithm: subdomain CG to "
-                                            f"{MIXED_INNER_RTOL:g} of each iteration's defect")
+                                            f"{tin:g} of each iteration's defect")
         line["fp64_refine"]["roofline"] = f["roofline_dominant"]
         if head == "mixed":
             line["mixed_speedup_vs_fp64_refine"] = round(h["value"] / f["value"], 3)
@@ -824,6 +835,8 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the mixed inner tolerance at its default instead of tuning it")
     ap.add_argument("--no-oracle", action="store_true",
                     help="skip the oracle's monolithic solve (the error of each line against it)")
     ap.add_argument("--prec", choices=("both", "mixed", "fp64"), default="both")
