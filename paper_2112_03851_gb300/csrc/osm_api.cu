@@ -28,8 +28,8 @@
 using namespace osm;
 
 // z-chunk lengths the autotuner tries for the tensor kernel (the last one
-// leaves every box whole).
-constexpr int kZChunks[4] = {8, 16, 32, 1 << 20};
+// leaves every box of up to 128 planes whole).
+constexpr int kZChunks[4] = {8, 16, 32, 128};
 
 struct osm_ctx {
   HostProblem hp;
@@ -166,6 +166,8 @@ osm_status upload_problem(osm_ctx* h) {
   for (double** v : {&st.rho, &st.alpha, &st.beta, &st.bb, &st.rr}) OSM_CUDA(h, dalloc(h, v, ns));
   for (int32_t** v : {&st.active, &st.iters, &st.status}) OSM_CUDA(h, dalloc(h, v, ns));
   OSM_CUDA(h, dalloc(h, &st.ucnt, ns));
+  OSM_CUDA(h, dalloc(h, &st.tcnt, ns));
+  OSM_CUDA(h, dalloc(h, &st.pq, ns));
   OSM_CUDA(h, dalloc(h, &st.sc, ns));
   OSM_CUDA(h, dalloc(h, &st.isc2, ns));
   // the tensor form of the FP32 operator (mixed handles): box layout tables

@@ -190,6 +190,8 @@ struct DevSubState {
   int32_t* iters;   // CG iterations of the current solve
   int32_t* status;  // 0 ok, 1 cap reached, 2 breakdown
   unsigned* ucnt;   // per-subdomain ticket of the CG update's blocks (reset by the last)
+  unsigned* tcnt;   // per-subdomain ticket of the tensor kernel's CTAs (reset by the last)
+  double* pq;       // p.q of the current CG step (set by the tensor kernel's last CTA)
   float* sc;        // FP32 inner solve: power of two applied to both factors
                     // of every FP32 dot product (keeps r*r out of underflow)
   double* isc2;     // 1 / sc^2, undoes that scaling on the warp partials
@@ -288,6 +290,9 @@ struct DevProblem {
   // Range table of the p.q partials of the CG step's SpMV kernel (sub_tile0
   // for the SELL kernels; sub_cta0 for the tensor kernel).
   const int64_t* sub_part0;
+  // 1: the CG step's SpMV kernel already formed p.q and alpha per subdomain
+  // (st.pq, st.alpha); 0: the update kernel adds the p.q partials itself
+  int32_t alpha_ready;
   // FP32 inner solve on the tensor-product operator in the box layout (t32 =
   // 1; else the FP32 SELL operator in the vector-row layout).  The x32 .. q32
   // vectors then hold box rows, dinv32b is the box-layout Jacobi diagonal.

@@ -211,8 +211,13 @@ __device__ __forceinline__ void cg_step_finish(DevProblem& d, const int64_t* __r
   const int64_t b0 = ub0[s], nb = ub0[s + 1] - b0;
   const double rz = warp_sum_parts(d.part1, b0, nb);
   const double rr = warp_sum_parts(d.part2, b0, nb);
-  const int64_t c0 = d.sub_part0[s];
-  const double pq = warp_sum_parts(d.part0, c0, d.sub_part0[s + 1] - c0);
+  double pq;
+  if (d.alpha_ready) {
+    pq = d.st.pq[s];
+  } else {
+    const int64_t c0 = d.sub_part0[s];
+    pq = warp_sum_parts(d.part0, c0, d.sub_part0[s + 1] - c0);
+  }
   if (lane == 0) {
     const int it = d.st.iters[s] + 1;
     d.st.iters[s] = it;
@@ -344,9 +349,14 @@ __global__ void __launch_bounds__(kTileRows) k_cg_update_a(DevProblem d, CgVec<T
       di[j] = v.dinv[row];
     }
   }
-  const int64_t c0 = d.sub_part0[s];
-  const double pq = warp_sum_parts(d.part0, c0, d.sub_part0[s + 1] - c0);
-  const T alpha = (pq > 0.0 && isfinite(pq)) ? (T)(d.st.rho[s] / pq) : T(0);
+  T alpha;
+  if (d.alpha_ready) {
+    alpha = (T)d.st.alpha[s];
+  } else {
+    const int64_t c0 = d.sub_part0[s];
+    const double pq = warp_sum_parts(d.part0, c0, d.sub_part0[s + 1] - c0);
+    alpha = (pq > 0.0 && isfinite(pq)) ? (T)(d.st.rho[s] / pq) : T(0);
+  }
   const T sc = sizeof(T) == 4 ? (T)d.st.sc[s] : T(1);
   T a = T(0), b = T(0);
 #pragma unroll
@@ -411,6 +421,115 @@ __global__ void __launch_bounds__(kTileRows) k_cg_update_a(DevProblem d, CgVec<T
   if (!s_last || warp != 0) return;
   __threadfence();
   cg_step_finish(d, ub0, s, lane);
+  if (lane == 0) cg_step_arrive(d, cond, use_cond);
+}
+
+// The FP32 update of the mixed form's inner CG with 16-byte accesses: the
+// same arithmetic as k_cg_update_a<float, kUpdGroup> (alpha, x += alpha p,
+// r -= alpha q, z = D^-1 r, scaled r.z and r.r per block, the subdomain's
+// last block finishing the step), but a thread owns 4 consecutive rows per
+// 1024-row half of the block's 2048 rows and moves each vector's values with
+// one float4 load or store: a quarter of the load and store instructions.
+__global__ void __launch_bounds__(kTileRows) k_cg_update32(DevProblem d, CgVec<float> v, unsigned long long cond,
+                                                           int use_cond) {
+  constexpr int G = kUpdGroup;
+  constexpr int H = G * kTileRows / (4 * kTileRows);   // float4 groups per thread (2)
+  __shared__ double sm[2][kTileSlices];
+  __shared__ bool s_last;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ub = blockIdx.x;
+  const int64_t t0 = d.ub_tile0[ub];
+  const int s = d.tile_sub[t0];
+  const int64_t ts0 = d.sub_tile0[s];
+  if (!d.st.active[s]) {
+    if (t0 == ts0 && threadIdx.x == 0) cg_step_arrive(d, cond, use_cond);
+    return;
+  }
+  const int64_t nrows = min((int64_t)G, d.sub_tile0[s + 1] - t0) * kTileRows;
+  const int64_t r0 = t0 * kTileRows;
+  float4 pr[H], xr[H], qr[H], rr0[H], di[H];
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    const int64_t o = 4 * (int64_t)threadIdx.x + (int64_t)h * 4 * kTileRows;
+    if (o < nrows) {
+      pr[h] = *reinterpret_cast<const float4*>(v.p + r0 + o);
+      xr[h] = *reinterpret_cast<const float4*>(v.x + r0 + o);
+      qr[h] = *reinterpret_cast<const float4*>(v.q + r0 + o);
+      rr0[h] = *reinterpret_cast<const float4*>(v.r + r0 + o);
+      di[h] = *reinterpret_cast<const float4*>(v.dinv + r0 + o);
+    }
+  }
+  float alpha;
+  if (d.alpha_ready) {
+    alpha = (float)d.st.alpha[s];
+  } else {
+    const int64_t c0 = d.sub_part0[s];
+    const double pq = warp_sum_parts(d.part0, c0, d.sub_part0[s + 1] - c0);
+    alpha = (pq > 0.0 && isfinite(pq)) ? (float)(d.st.rho[s] / pq) : 0.f;
+  }
+  const float sc = d.st.sc[s];
+  float a = 0.f, b = 0.f;
+#pragma unroll
+  for (int h = 0; h < H; ++h) {
+    const int64_t o = 4 * (int64_t)threadIdx.x + (int64_t)h * 4 * kTileRows;
+    if (o < nrows) {
+      float4 x, r, z;
+      x.x = fmaf(alpha, pr[h].x, xr[h].x);
+      x.y = fmaf(alpha, pr[h].y, xr[h].y);
+      x.z = fmaf(alpha, pr[h].z, xr[h].z);
+      x.w = fmaf(alpha, pr[h].w, xr[h].w);
+      r.x = fmaf(-alpha, qr[h].x, rr0[h].x);
+      r.y = fmaf(-alpha, qr[h].y, rr0[h].y);
+      r.z = fmaf(-alpha, qr[h].z, rr0[h].z);
+      r.w = fmaf(-alpha, qr[h].w, rr0[h].w);
+      z.x = di[h].x * r.x;
+      z.y = di[h].y * r.y;
+      z.z = di[h].z * r.z;
+      z.w = di[h].w * r.w;
+      *reinterpret_cast<float4*>(v.x + r0 + o) = x;
+      *reinterpret_cast<float4*>(v.r + r0 + o) = r;
+      *reinterpret_cast<float4*>(v.z + r0 + o) = z;
+      const float rs0 = r.x * sc, rs1 = r.y * sc, rs2 = r.z * sc, rs3 = r.w * sc;
+      a = fmaf(rs0, z.x * sc, a);
+      a = fmaf(rs1, z.y * sc, a);
+      a = fmaf(rs2, z.z * sc, a);
+      a = fmaf(rs3, z.w * sc, a);
+      b = fmaf(rs0, rs0, b);
+      b = fmaf(rs1, rs1, b);
+      b = fmaf(rs2, rs2, b);
+      b = fmaf(rs3, rs3, b);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) {
+    const double isc2 = d.st.isc2[s];
+    sm[0][warp] = (double)a * isc2;
+    sm[1][warp] = (double)b * isc2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int w = 0; w < kTileSlices; ++w) {
+      s0 += sm[0][w];
+      s1 += sm[1][w];
+    }
+    d.part1[ub] = s0;
+    d.part2[ub] = s1;
+    __threadfence();   // publish the partials before the ticket
+    const unsigned nblk = (unsigned)(d.sub_ub0[s + 1] - d.sub_ub0[s]);
+    const unsigned t = atomicAdd(&d.st.ucnt[s], 1u);
+    s_last = t == nblk - 1u;
+    if (s_last) d.st.ucnt[s] = 0u;
+  }
+  __syncthreads();
+  if (!s_last || warp != 0) return;
+  __threadfence();
+  cg_step_finish(d, d.sub_ub0, s, lane);
   if (lane == 0) cg_step_arrive(d, cond, use_cond);
 }
 
@@ -768,12 +887,12 @@ cudaError_t launch_cg_iteration32(const DevProblem& d, cudaStream_t s, unsigned 
     cudaError_t e = launch_tensor_dir32(b, s);
     if (e != cudaSuccess) return e;
     const CgVec<float> v{b.x32, b.r32, b.z32, b.p32, b.q32, b.dinv32b, b.vals32};
-    k_cg_update_a<float, kUpdGroup><<<(unsigned)b.n_ublocks, kTileRows, 0, s>>>(b, v, cond, use_cond);
+    k_cg_update32<<<(unsigned)b.n_ublocks, kTileRows, 0, s>>>(b, v, cond, use_cond);
     return cudaGetLastError();
   }
   OSM_LAUNCH_RPL(d.rpl32, d.c16_32, k_cg_spmv_dir32, s, d);
   const CgVec<float> v{d.x32, d.r32, d.z32, d.p32, d.q32, d.dinv32, d.vals32};
-  k_cg_update_a<float, kUpdGroup><<<(unsigned)d.n_ublocks, kTileRows, 0, s>>>(d, v, cond, use_cond);
+  k_cg_update32<<<(unsigned)d.n_ublocks, kTileRows, 0, s>>>(d, v, cond, use_cond);
   return cudaGetLastError();
 }
 

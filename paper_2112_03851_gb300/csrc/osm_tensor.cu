@@ -39,6 +39,8 @@ constexpr int kTxPre = (kTxPlane + kTileRows - 1) / kTileRows;
 constexpr int kTxY = (kTxRows + kTileRows - 1) / kTileRows;
 constexpr int kTxMaxRows = kTileRows / 3 + 2;   // rows 256 columns can touch (boxes are >= 3 nodes wide)
 constexpr int kTxStages = 4;                     // input planes in flight
+constexpr int kTxRowsP = 640;                    // >= (256 / nx + 2) (nx + 4) for 3 <= nx <= 128
+constexpr int kTxMaxZ = 128;                     // output planes per CTA (z chunks are at most this long)
 
 // FP32 bands of every subdomain: the mass as it is, the stiffness with the
 // transmission term p of each interface side added at that side's end node
@@ -81,28 +83,33 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // MODE 0: one step of the FP32 inner CG (the tensor counterpart of
 // k_cg_spmv_dir32): t = A z, then p = z + beta p, q = t + beta q (first step
 // beta = 0: p = z, q = t) and the CTA's partial of p.q (scaled FP32 dots as in
-// the SELL kernel) into part0[cta].  MODE 1: y = A x (x, y in the box layout).
+// the SELL kernel) into part0[cta]; the subdomain's last CTA (a ticket, no
+// waiting) adds the partials in a fixed order and stores p.q and alpha = r.z
+// / p.q for the update kernel.  MODE 1: y = A x (x, y in the box layout).
 // A CTA covers 256 (x, y) columns of one box and one chunk of its z range
 // (box_dims: the chunk length and the number of column blocks), marching
 // over the chunk's planes and the two halo planes on either side.  The input
 // planes stream through kTxStages shared-memory stages filled by
 // asynchronous copies issued kTxStages - 1 planes ahead, together with the
-// old p and q of the output plane they complete; the z bands are loaded one
-// plane ahead.
+// old p and q of the output plane they complete.  The plane loop is unrolled
+// by five, so the five-plane rings of the partial products live in fixed
+// registers.
 template <int MODE>
 __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const float* __restrict__ xin,
                                                            float* __restrict__ yout) {
   __shared__ __align__(16) float S[kTxStages][kTxPlane];
   __shared__ float PQ[MODE == 0 ? kTxStages : 1][2][MODE == 0 ? kTileRows : 1];   // old p, q of an output plane
-  __shared__ float TM[kTxRows], TK[kTxRows];
-  __shared__ float CY[kTxMaxRows][10];   // y bands of the CTA's rows: M then K~
+  __shared__ float TM[kTxRowsP], TK[kTxRowsP];   // y-pass rows, two zero columns either side
+  __shared__ float CY[kTxMaxRows][10];           // y bands of the CTA's rows: M then K~
+  __shared__ float CZ[kTxMaxZ][10];              // z bands of the chunk's output planes
   __shared__ double red[kTileSlices];
+  __shared__ bool s_last;
   const int cta = blockIdx.x;
   const int s = d.cta_sub[cta];
   if (MODE == 0 && !d.st.active[s]) return;
   const int* dims = d.box_dims + kBoxDims * s;
   const int nx = dims[0], ny = dims[1], nz = dims[2], fm = dims[3], zc = dims[4], ncb = dims[5];
-  const int nxy = nx * ny;
+  const int nxy = nx * ny, nxp = nx + 4;
   const int64_t voff = d.box_voff[s];
   const int local = (int)(cta - d.sub_cta0[s]);
   const int c0 = (local % ncb) * kTileRows;
@@ -118,6 +125,16 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
   for (int t = threadIdx.x; t < 5 * nrow; t += kTileRows) {
     CY[t / 5][t % 5] = cM[by + 5 * (int64_t)jlo + t];
     CY[t / 5][5 + t % 5] = cK[by + 5 * (int64_t)jlo + t];
+  }
+  for (int t = threadIdx.x; t < 5 * (k1 - k0); t += kTileRows) {
+    CZ[t / 5][t % 5] = cM[bz + 5 * (int64_t)k0 + t];
+    CZ[t / 5][5 + t % 5] = cK[bz + 5 * (int64_t)k0 + t];
+  }
+  for (int t = threadIdx.x; t < 4 * nrow; t += kTileRows) {   // the zero columns of TM, TK
+    const int r = t >> 2, c = t & 3;
+    const int at = r * nxp + (c < 2 ? c : nx + c);
+    TM[at] = 0.f;
+    TK[at] = 0.f;
   }
   float kx[5], mx[5];
 #pragma unroll
@@ -140,12 +157,16 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
       goff[m] = (jj >= 0 && jj < ny) ? (idx - r * nx) + nx * jj : -1;
     }
   }
-  int yrow[kTxY];
+  // y-pass slots: output row (in the CTA's rows) and padded TM index
+  int yrow[kTxY], ypad[kTxY];
 #pragma unroll
   for (int m = 0; m < kTxY; ++m) {
     const int idx = (int)threadIdx.x + m * kTileRows;
     yrow[m] = idx < ntr ? idx / nx : -1;
+    ypad[m] = yrow[m] >= 0 ? yrow[m] * nxp + 2 + (idx - yrow[m] * nx) : 0;
   }
+  const int xbase = (j - jlo) * nxp + i;   // TM index of this column's neighbour i - 2
+  const int zown = (j - jlo + 2) * nx + i;  // this column in the staged plane
   const float* __restrict__ src = MODE == 0 ? d.z32 : xin;
   float beta = 0.f, sc = 1.f;
   bool first = true;
@@ -173,97 +194,84 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
     }
     cp_async_commit();
   };
-  // z bands of an output plane, fetched one plane ahead
-  float zb[5], kb[5];
-  auto fetch_out = [&](int k) {
-    if (k < k0 || k >= k1) return;
-    const int64_t cz = bz + 5 * (int64_t)k;
-#pragma unroll
-    for (int c = 0; c < 5; ++c) { zb[c] = cM[cz + c]; kb[c] = cK[cz + c]; }
-  };
   float ph[5], qh[5], zh[5];
 #pragma unroll
-  for (int c = 0; c < 5; ++c) { ph[c] = 0.f; qh[c] = 0.f; zh[c] = 0.f; zb[c] = 0.f; kb[c] = 0.f; }
+  for (int c = 0; c < 5; ++c) { ph[c] = 0.f; qh[c] = 0.f; zh[c] = 0.f; }
   float vv = 0.f;
 #pragma unroll
   for (int st = 0; st < kTxStages - 1; ++st) issue(k0 - 2 + st, st);
-  fetch_out(k0);
   int st = 0;
-  for (int kk = k0 - 2; kk < k1 + 2; ++kk) {
-    // plane kk + stages - 1 into the stage freed at the end of the last plane
-    issue(kk + kTxStages - 1, st == 0 ? kTxStages - 1 : st - 1);
-    cp_async_wait<kTxStages - 1>();   // this thread's copies of plane kk have landed
-    __syncthreads();                  // ... and every other thread's
-    const bool pin = kk >= 0 && kk < nz;
-    float zc_own = 0.f;
-    if (pin) {
-      // y pass: My z and K~y z on the CTA's rows, every x
+  for (int kb = k0 - 2; kb < k1 + 2; kb += 5) {
 #pragma unroll
-      for (int m = 0; m < kTxY; ++m) {
-        if (yrow[m] >= 0) {
-          const int idx = (int)threadIdx.x + m * kTileRows;
-          const float* cy = CY[yrow[m]];
-          float sm = 0.f, sk = 0.f;
+    for (int u = 0; u < 5; ++u) {
+      const int kk = kb + u;
+      if (kk < k1 + 2) {   // uniform across the CTA
+        // plane kk + stages - 1 into the stage freed at the end of the last plane
+        issue(kk + kTxStages - 1, st == 0 ? kTxStages - 1 : st - 1);
+        cp_async_wait<kTxStages - 1>();   // this thread's copies of plane kk have landed
+        __syncthreads();                  // ... and every other thread's
+        const bool pin = kk >= 0 && kk < nz;
+        float zc_own = 0.f;
+        if (pin) {
+          // y pass: My z and K~y z on the CTA's rows, every x
 #pragma unroll
-          for (int b = 0; b < 5; ++b) {
-            const float v = S[st][idx + b * nx];
-            sm = fmaf(cy[b], v, sm);
-            sk = fmaf(cy[5 + b], v, sk);
+          for (int m = 0; m < kTxY; ++m) {
+            if (yrow[m] >= 0) {
+              const int idx = (int)threadIdx.x + m * kTileRows;
+              const float* cy = CY[yrow[m]];
+              float sm = 0.f, sk = 0.f;
+#pragma unroll
+              for (int b = 0; b < 5; ++b) {
+                const float v = S[st][idx + b * nx];
+                sm = fmaf(cy[b], v, sm);
+                sk = fmaf(cy[5 + b], v, sk);
+              }
+              TM[ypad[m]] = sm;
+              TK[ypad[m]] = sk;
+            }
           }
-          TM[idx] = sm;
-          TK[idx] = sk;
+          if (valid) zc_own = S[st][zown];
         }
-      }
-      if (valid) zc_own = S[st][(j - jlo + 2) * nx + i];
-    }
-    __syncthreads();   // TM, TK complete; stage st is free for the next issue
-    // x pass for this thread's column: P = K~x (My z) + Mx (K~y z), Q = Mx (My z)
-    float P = 0.f, Q = 0.f;
-    if (pin && valid) {
-      const int base = (j - jlo) * nx + i;
+        __syncthreads();   // TM, TK complete; stage st is free for the next issue
+        // x pass for this thread's column: P = K~x (My z) + Mx (K~y z), Q = Mx (My z)
+        float P = 0.f, Q = 0.f;
+        if (pin && valid) {
 #pragma unroll
-      for (int a = 0; a < 5; ++a) {
-        const int ii = i + a - 2;
-        if (ii >= 0 && ii < nx) {
-          const float tm = TM[base + a - 2], tk = TK[base + a - 2];
-          P = fmaf(kx[a], tm, fmaf(mx[a], tk, P));
-          Q = fmaf(mx[a], tm, Q);
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 4; ++c) { ph[c] = ph[c + 1]; qh[c] = qh[c + 1]; zh[c] = zh[c + 1]; }
-    ph[4] = P;
-    qh[4] = Q;
-    zh[4] = zc_own;
-    const int k = kk - 2;   // output plane: its neighbours k-2 .. k+2 are in the rings
-    if (k >= k0) {
-      float zb_k[5], kb_k[5];
-#pragma unroll
-      for (int c = 0; c < 5; ++c) { zb_k[c] = zb[c]; kb_k[c] = kb[c]; }
-      fetch_out(k + 1);
-      if (valid) {
-        float t = 0.f;
-#pragma unroll
-        for (int c = 0; c < 5; ++c) t = fmaf(zb_k[c], ph[c], fmaf(kb_k[c], qh[c], t));
-        if (dcol || ((fm & 16) && k == 0) || ((fm & 32) && k == nz - 1)) t = 0.f;
-        const int64_t row = voff + col + (int64_t)nxy * k;
-        if (MODE == 0) {
-          const float z = zh[2];
-          float p = z, q = t;
-          if (!first) {   // this thread's own staged values: no barrier needed
-            p = fmaf(beta, PQ[st][0][threadIdx.x], z);
-            q = fmaf(beta, PQ[st][1][threadIdx.x], t);
+          for (int a = 0; a < 5; ++a) {
+            const float tm = TM[xbase + a], tk = TK[xbase + a];
+            P = fmaf(kx[a], tm, fmaf(mx[a], tk, P));
+            Q = fmaf(mx[a], tm, Q);
           }
-          d.p32[row] = p;
-          d.q32[row] = q;
-          vv = fmaf(p * sc, q * sc, vv);
-        } else {
-          yout[row] = t;
         }
+        // ring slot u holds plane kk; slot (u + 1 + c) % 5 holds plane kk - 4 + c
+        ph[u] = P;
+        qh[u] = Q;
+        zh[u] = zc_own;
+        const int k = kk - 2;   // output plane: its neighbours k-2 .. k+2 are in the rings
+        if (k >= k0 && valid) {
+          const float* cz = CZ[k - k0];
+          float t = 0.f;
+#pragma unroll
+          for (int c = 0; c < 5; ++c) t = fmaf(cz[c], ph[(u + 1 + c) % 5], fmaf(cz[5 + c], qh[(u + 1 + c) % 5], t));
+          if (dcol || ((fm & 16) && k == 0) || ((fm & 32) && k == nz - 1)) t = 0.f;
+          const int64_t row = voff + col + (int64_t)nxy * k;
+          if (MODE == 0) {
+            const float z = zh[(u + 3) % 5];
+            float p = z, q = t;
+            if (!first) {   // this thread's own staged values: no barrier needed
+              p = fmaf(beta, PQ[st][0][threadIdx.x], z);
+              q = fmaf(beta, PQ[st][1][threadIdx.x], t);
+            }
+            d.p32[row] = p;
+            d.q32[row] = q;
+            vv = fmaf(p * sc, q * sc, vv);
+          } else {
+            yout[row] = t;
+          }
+        }
+        st = st + 1 == kTxStages ? 0 : st + 1;
       }
     }
-    st = st + 1 == kTxStages ? 0 : st + 1;
   }
   cp_async_wait<0>();   // no copy outlives the CTA
   if (MODE == 0) {
@@ -277,6 +285,22 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
 #pragma unroll
       for (int w = 0; w < kTileSlices; ++w) acc += red[w];
       d.part0[cta] = acc;
+      // the subdomain's last CTA forms p.q and alpha (a ticket, not a wait)
+      __threadfence();
+      const unsigned nct = (unsigned)(d.sub_cta0[s + 1] - d.sub_cta0[s]);
+      const unsigned t = atomicAdd(&d.st.tcnt[s], 1u);
+      s_last = t == nct - 1u;
+      if (s_last) d.st.tcnt[s] = 0u;
+    }
+    __syncthreads();
+    if (s_last && warp == 0) {
+      __threadfence();
+      const int64_t a0 = d.sub_cta0[s];
+      const double pq = warp_sum_parts(d.part0, a0, d.sub_cta0[s + 1] - a0);
+      if (lane == 0) {
+        d.st.pq[s] = pq;
+        d.st.alpha[s] = (pq > 0.0 && isfinite(pq)) ? d.st.rho[s] / pq : 0.0;
+      }
     }
   }
 }
@@ -292,6 +316,7 @@ DevProblem fp32_view(const DevProblem& d) {
   v.ub_tile0 = d.box_ub_tile0;
   v.sub_ub0 = d.box_sub_ub0;
   v.n_ublocks = d.box_n_ublocks;
+  v.alpha_ready = 1;   // the tensor kernel's last CTA per subdomain forms p.q and alpha
   v.sub_part0 = d.sub_cta0;
   return v;
 }
