@@ -120,7 +120,10 @@ typedef struct {
                                zeroth-order transmission (q = 0) only: with q != 0 the
                                handle uses the SELL matrix.  Boxes wider than 128 nodes
                                along x also keep the SELL matrix. */
-    int32_t reserved;
+    int32_t fp64_start;     /* OSM_MIXED with the tensor form: the kernel of each
+                               refinement step's FP64 defect d = b - A u.  0 (default):
+                               chosen by the autotuner; 1: the SELL SpMV; 2: the FP64
+                               tensor-product kernel on a box-layout copy of u */
 } osm_opts;
 
 typedef struct {
@@ -153,8 +156,15 @@ typedef struct {
     int32_t tensor_zchunk;       /* z planes per CTA of the tensor kernel (0: no tensor form);
                                     2^20 leaves every subdomain box whole */
     int32_t reserved_i;
-    double tensor_ms_zchunk[4];  /* autotuner timings with z chunks of 8, 16, 32 planes and
-                                    whole boxes (ms, 0 if not run) */
+    double tensor_ms_zchunk[4];  /* autotuner timings with z chunks of 8, 16, 32 and 128 planes
+                                    (ms, 0 if not run) */
+    int32_t fp64_start;          /* OSM_MIXED: kernel of each refinement step's FP64 defect
+                                    d = b - A u: 1 the SELL SpMV, 2 the FP64 tensor-product
+                                    kernel (chosen by the autotuner with the tensor form); 0
+                                    otherwise */
+    int32_t reserved_j;
+    double start_ms[2];          /* autotuner timings of that step: SELL, tensor (ms, 0 if not
+                                    run) */
     int64_t box_rows;            /* rows of the box layout of the tensor form (0 if none) */
 } osm_info_t;
 

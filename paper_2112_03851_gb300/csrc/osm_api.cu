@@ -59,6 +59,8 @@ struct osm_ctx {
   // tensor-product FP32 operator (mixed handles whose boxes fit the kernel)
   bool have_box = false;
   int fp32_tuned = 1;           // 1: SELL, 2: tensor product (autotuner or opts.fp32_operator)
+  int init_tuned = 0;           // 1: the mixed refinement step starts with the FP64 tensor kernel
+  double tune_init_ms[2] = {};  // autotuner timings of the FP64 refinement start: SELL, tensor
   int zchunk = kZChunks[1];     // z planes per CTA of the tensor kernel (autotuned)
   double tune_tensor_ms = 0.0;
   double tune_zchunk_ms[4] = {};
@@ -178,6 +180,7 @@ osm_status upload_problem(osm_ctx* h) {
   const size_t nparts = h->have_box ? (size_t)std::max({hp.n_tiles, hp.box_tiles, hp.box_ctas}) : (size_t)hp.n_tiles;
   for (double** v : {&d.part0, &d.part1, &d.part2}) OSM_CUDA(h, dalloc(h, v, nparts));
   d.sub_part0 = sub_tile0;
+  d.sub_init0 = sub_tile0;
   // interface rows
   d.n_irow = (int32_t)hp.irow.size();
   int32_t *irow, *irow_sub, *ilam_ptr, *ilam, *im_ptr, *im_col;
@@ -226,8 +229,10 @@ osm_status upload_problem(osm_ctx* h) {
   OSM_CUDA(h, dalloc(h, &d.lam, 2 * (size_t)hp.n_fent));
   // interface-column layer of K_i (stop test)
   d.n_lrow = (int32_t)hp.li_row.size();
-  int32_t *li_row, *li_ptr, *li_col;
+  int32_t *li_row, *li_ptr, *li_col, *li_irow;
   double* li_val;
+  OSM_CUDA(h, upload(h, &li_irow, hp.li_irow));
+  d.li_irow = li_irow;
   OSM_CUDA(h, upload(h, &li_row, hp.li_row));
   OSM_CUDA(h, upload(h, &li_ptr, hp.li_ptr));
   OSM_CUDA(h, upload(h, &li_col, hp.li_col));
@@ -299,6 +304,13 @@ osm_status upload_problem(osm_ctx* h) {
       d.band_k = bk; d.band_m = bm;
       OSM_CUDA(h, dalloc(h, &d.cK32, hp.band_k.size()));
       OSM_CUDA(h, dalloc(h, &d.cM32, hp.band_m.size()));
+      int32_t* box_vec;
+      OSM_CUDA(h, upload(h, &box_vec, hp.box_vec));
+      d.box_vec = box_vec;
+      OSM_CUDA(h, dalloc(h, &d.ub, hp.box_rows));
+      OSM_CUDA(h, dalloc(h, &d.cK64, hp.band_k.size()));
+      OSM_CUDA(h, dalloc(h, &d.cM64, hp.band_m.size()));
+      OSM_CUDA(h, tensor_kernel_setup());
       std::vector<float> dib(hp.box_rows, 0.f);
       for (int64_t r = 0; r < hp.vec_rows; ++r)
         if (hp.row_box[r] >= 0) dib[hp.row_box[r]] = (float)hp.dinv0[r];
@@ -365,9 +377,16 @@ osm_status select_fp32_operator(osm_ctx* h) {
   for (size_t s = 0; s < h->tc_host.size() / 4; ++s)
     if (h->tc_host[4 * s + 1] != 0.0 || h->tc_host[4 * s + 3] != 0.0) q_zero = false;
   const int want = (h->have_box && h->fp32_tuned == 2 && q_zero) ? 1 : 0;
-  if (want == h->d.t32) return OSM_OK;
+  const int want_init = want && h->init_tuned;
+  if (want == h->d.t32 && want_init == h->d.t64i) return OSM_OK;
+  const bool layout_change = want != h->d.t32;
+  const bool mirror = want_init && !h->d.t64i;
   h->d.t32 = want;
+  h->d.t64i = want_init;
+  if (mirror) OSM_CUDA(h, launch_box_mirror(h->d, h->stream));   // ub from the current iterate
+  h->d.sub_init0 = want_init ? h->d.sub_cta0 : h->d.sub_tile0;
   drop_graphs(h);
+  if (!layout_change) return OSM_OK;
   const size_t n32 = std::max<size_t>((size_t)h->hp.vec_rows, (size_t)h->hp.box_rows);
   for (float* v : {h->d.x32, h->d.r32, h->d.z32, h->d.p32, h->d.q32})
     OSM_CUDA(h, cudaMemsetAsync(v, 0, sizeof(float) * n32, h->stream));
@@ -562,6 +581,7 @@ osm_status autotune_spmv(osm_ctx* h) {
   h->d.c16_64 = have16;
   h->d.c16_32 = have16 && mixed;
   h->fp32_tuned = (mixed && h->have_box && h->opts.fp32_operator == 2) ? 2 : 1;
+  h->init_tuned = (mixed && h->have_box && h->opts.fp64_start == 2) ? 1 : 0;
   if (h->opts.autotune != 1) return select_fp32_operator(h);
   h->d.t32 = 0;   // the SELL variants first (vectors are zero: no layout to clear)
   OSM_CUDA(h, launch_profile_state(h->d, h->stream));
@@ -617,6 +637,25 @@ osm_status autotune_spmv(osm_ctx* h) {
     }
     if (e == cudaSuccess) e = set_zchunk(h, best_zc);
     h->tune_tensor_ms = best_t;
+    // the mixed refinement step's FP64 start: SELL SpMV or FP64 tensor kernel
+    // (the partial tables follow the kernel); the faster one serves whenever
+    // the tensor layout is in use
+    for (int t = 0; t < 2 && e == cudaSuccess; ++t) {
+      h->d.t64i = t;
+      h->d.sub_init0 = t ? h->d.sub_cta0 : h->d.sub_tile0;
+      for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = launch_cg_start(h->d, h->stream, 1);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+      for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = launch_cg_start(h->d, h->stream, 1);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      h->tune_init_ms[t] = ms / 5.0;
+    }
+    h->init_tuned = h->opts.fp64_start == 2 ? 1 : h->opts.fp64_start == 1 ? 0
+                                                : (h->tune_init_ms[1] < h->tune_init_ms[0] ? 1 : 0);
+    h->d.t64i = 0;
+    h->d.sub_init0 = h->d.sub_tile0;
     h->d.t32 = 0;
     if (e == cudaSuccess && h->opts.fp32_operator == 0 && best_t < best_sell32) h->fp32_tuned = 2;
   }
@@ -852,6 +891,7 @@ osm_status run_sample_batch(osm_ctx* h, int nb, const double* p, double rtol, in
 
 osm_status reset_state(osm_ctx* h) {
   OSM_CUDA(h, cudaMemsetAsync(h->d.x, 0, sizeof(double) * h->hp.vec_rows, h->stream));
+  if (h->d.ub) OSM_CUDA(h, cudaMemsetAsync(h->d.ub, 0, sizeof(double) * h->hp.box_rows, h->stream));
   if (h->hp.n_fent) OSM_CUDA(h, cudaMemsetAsync(h->d.lam, 0, sizeof(double) * 2 * h->hp.n_fent, h->stream));
   return OSM_OK;
 }
@@ -915,7 +955,7 @@ osm_status osm_setup(const osm_mesh* mesh, const double* drho, const osm_decomp*
   if (!h) return OSM_E_NOMEM;
   if (opts) h->opts = *opts; else osm_default_opts(&h->opts);
   if (!(h->opts.inner_rtol > 0.0) || h->opts.max_outer < 1 || h->opts.max_inner < 1 || h->opts.max_seconds < 1 ||
-      h->opts.fp32_operator < 0 || h->opts.fp32_operator > 2) {
+      h->opts.fp32_operator < 0 || h->opts.fp32_operator > 2 || h->opts.fp64_start < 0 || h->opts.fp64_start > 2) {
     delete h;
     return OSM_E_ARG;
   }
@@ -985,6 +1025,9 @@ osm_status osm_info(osm_handle h, osm_info_t* o) {
   o->fp32_operator_tuned = h->opts.prec == OSM_MIXED ? h->fp32_tuned : 0;
   o->tensor_ms_fp32 = h->tune_tensor_ms;
   o->tensor_zchunk = h->have_box ? h->zchunk : 0;
+  o->fp64_start = h->opts.prec == OSM_MIXED ? (h->d.t64i ? 2 : 1) : 0;
+  o->start_ms[0] = h->tune_init_ms[0];
+  o->start_ms[1] = h->tune_init_ms[1];
   for (int c = 0; c < 4; ++c) o->tensor_ms_zchunk[c] = h->tune_zchunk_ms[c];
   o->box_rows = h->have_box ? h->hp.box_rows : 0;
   return OSM_OK;
@@ -1079,7 +1122,7 @@ osm_status osm_setup_batch(int32_t n_inst, const osm_mesh* meshes, const double*
   if (!(h->opts.inner_rtol > 0.0) || h->opts.max_outer < 1 || h->opts.max_inner < 1 || h->opts.max_seconds < 1 ||
       (h->opts.prec != OSM_FP64 && h->opts.prec != OSM_MIXED && h->opts.prec != OSM_FP64_REFINE) ||
       (h->opts.prec != OSM_FP64 && !(h->opts.mixed_inner_rtol > 0.0 && h->opts.mixed_inner_rtol < 1.0)) ||
-      h->opts.fp32_operator < 0 || h->opts.fp32_operator > 2)
+      h->opts.fp32_operator < 0 || h->opts.fp32_operator > 2 || h->opts.fp64_start < 0 || h->opts.fp64_start > 2)
     return fail(h, OSM_E_ARG, "osm_setup_batch: bad options");
   h->stream = (cudaStream_t)cuda_stream;
   auto t0 = std::chrono::steady_clock::now();
@@ -1234,12 +1277,11 @@ osm_status osm_stats(osm_handle h, osm_stats_t* o) {
   } else {
     // solve: once the nodal load, the first RHS gather and CG start; per
     // Schwarz iteration the CG finaliser, FP64 correction (mixed), exchange
-    // (if any face), the next RHS gather and CG start, average, face
-    // correction (if any interface), interface layer (if any), residual
-    // partials, residual finaliser; per CG step SpMV (+ direction epilogue in
-    // FP32) and update (+ the step's finish), plus the FP64 direction
-    const int64_t per_outer = 1 + mixed + faces + 2 + 1 + (h->hp.irow.empty() ? 0 : 1) +
-                              (h->hp.li_row.empty() ? 0 : 1) + 2;
+    // (if any face), the next RHS gather and CG start, average, interface
+    // layer (if any), residual partials, residual finaliser; per CG step SpMV
+    // (+ direction epilogue in FP32) and update (+ the step's finish), plus
+    // the FP64 direction
+    const int64_t per_outer = 1 + mixed + faces + 2 + 1 + (h->hp.li_row.empty() ? 0 : 1) + 2;
     o->n_launches = 3 + per_outer * c.n_outer + (mixed ? 2 : 3) * (int64_t)c.total_inner;
   }
   o->relres = c.relres;

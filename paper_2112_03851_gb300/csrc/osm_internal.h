@@ -126,6 +126,7 @@ struct HostProblem {
   std::vector<int32_t> box_cta_sub;
   std::vector<int64_t> box_sub_cta0;  // n_sub + 1
   std::vector<int32_t> row_box;       // vector row -> box row (-1: padding)
+  std::vector<int32_t> box_vec;       // box row -> vector row (-1: Dirichlet node or padding)
   int64_t box_rows = 0, box_tiles = 0, box_ctas = 0;
   int32_t box_max_nx = 0;
 
@@ -136,6 +137,7 @@ struct HostProblem {
   // vanishes off the interface rows.
   std::vector<int32_t> li_row, li_ptr, li_col;
   std::vector<double> li_val;
+  std::vector<int32_t> li_irow;       // per layer row: its interface-row index, or -1
 
   // Copies of each node of the full grid (vector rows, subdomain order).
   std::vector<int32_t> cp_ptr;        // n_nodes + 1
@@ -265,7 +267,7 @@ struct DevProblem {
   double* lam;
   // interface-column layer of K_i (HostProblem li_*)
   int32_t n_lrow;
-  const int32_t *li_row, *li_ptr, *li_col;
+  const int32_t *li_row, *li_ptr, *li_col, *li_irow;
   const double* li_val;
   // copies
   int64_t n_nodes;
@@ -311,6 +313,16 @@ struct DevProblem {
   const double *band_k, *band_m;        // plain 1-D bands (5 per band node)
   float *cK32, *cM32;                   // FP32 bands, stiffness with the Robin terms folded in
   float* dinv32b;
+  // FP64 tensor-product start of the mixed form's refinement step (t64i = 1,
+  // only with t32): the iterate u mirrored in the box layout (ub), the vector
+  // row of every box row (box_vec, -1: Dirichlet or padding), FP64 bands
+  int32_t t64i;
+  double* ub;
+  const int32_t* box_vec;
+  double *cK64, *cM64;
+  // partial range table of the CG start's ||r||^2, ||b||^2, r.z partials
+  // (sub_tile0 for the SELL kernels, sub_cta0 for the tensor start)
+  const int64_t* sub_init0;
   DevCtl* ctl;
   const int32_t* can2vec;
   int64_t n_local;
@@ -387,7 +399,6 @@ cudaError_t launch_profile_state(const DevProblem& d, cudaStream_t s);
 // Assembled nodal load and ||f||^2 partials for the stop test (once per solve).
 cudaError_t launch_load_nodes(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_cg_iteration32(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
-cudaError_t launch_cg_init_mixed(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
 cudaError_t launch_mixed_correct(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_apply32(const DevProblem& d, const double* x, double* y, cudaStream_t s);
 cudaError_t launch_spmv_plain32(const DevProblem& d, const float* x, float* y, cudaStream_t s);
@@ -396,6 +407,10 @@ cudaError_t launch_exchange(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_tensor_coef(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_tensor_dir32(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_tensor_apply32(const DevProblem& d, const float* x, float* y, cudaStream_t s);
+cudaError_t launch_tensor_init64(const DevProblem& d, cudaStream_t s);
+cudaError_t launch_box_mirror(const DevProblem& d, cudaStream_t s);
+// Shared-memory limits of the tensor kernels (once per process and device).
+cudaError_t tensor_kernel_setup();
 // The DevProblem seen by the FP32 CG kernels: the box layout's tile tables
 // when the tensor operator is in use, else d itself.
 DevProblem fp32_view(const DevProblem& d);
@@ -423,7 +438,6 @@ cudaError_t launch_mp_cg_iteration(const DevProblem& d, const DevSample& m, cuda
                                    unsigned long long cond, int use_cond, int mixed);
 cudaError_t launch_mp_exchange_residual(const DevProblem& d, const DevSample& m, cudaStream_t s,
                                         unsigned long long cond, int use_cond, int mixed);
-cudaError_t launch_residual(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);
 // CG start of the next Schwarz iteration (the SpMV kernel only: r = b - A u
 // or the FP64 defect, y = A u kept for the stop test) and its finaliser.
 cudaError_t launch_cg_start(const DevProblem& d, cudaStream_t s, int mixed);

@@ -169,10 +169,11 @@ __global__ void k_fin_init(DevProblem d, int mixed, unsigned long long cond, int
   // wall clock here; the ticket's fence publishes it to the last block
   if (blockIdx.x == 0 && threadIdx.x == 0 && d.ctl->t_start_ns == 0ull) d.ctl->t_start_ns = global_ns();
   if (s < d.n_sub) {
-    const int64_t t0 = d.sub_tile0[s], nt = d.sub_tile0[s + 1] - t0;
-    const double a0 = warp_sum_parts(d.part0, t0, nt);
-    const double a1 = warp_sum_parts(d.part1, t0, nt);
-    const double a2 = warp_sum_parts(d.part2, t0, nt);
+    const int64_t nt = d.sub_tile0[s + 1] - d.sub_tile0[s];      // the subdomain's 256-row tiles
+    const int64_t i0 = d.sub_init0[s], ni = d.sub_init0[s + 1] - i0;   // its CG-start partials
+    const double a0 = warp_sum_parts(d.part0, i0, ni);
+    const double a1 = warp_sum_parts(d.part1, i0, ni);
+    const double a2 = warp_sum_parts(d.part2, i0, ni);
     if (lane == 0) {
       d.st.rr[s] = a0;
       d.st.bb[s] = mixed ? a0 : a1;
@@ -592,10 +593,22 @@ __global__ void __launch_bounds__(kTileRows) k_mixed_correct(DevProblem d) {
   const int64_t row = blockIdx.x * (int64_t)kTileRows + threadIdx.x;
   if (d.t32) {
     const int32_t rb = d.row_box[row];
-    if (rb >= 0) d.x[row] += (double)d.x32[rb];
+    if (rb >= 0) {
+      const double u = d.x[row] + (double)d.x32[rb];
+      d.x[row] = u;
+      if (d.ub) d.ub[rb] = u;   // the box-layout mirror read by the tensor start
+    }
   } else {
     d.x[row] += (double)d.x32[row];
   }
+}
+
+// The iterate u copied into its box-layout mirror (when the FP64 tensor start
+// is switched on for a handle whose iterate is not zero).
+__global__ void __launch_bounds__(kTileRows) k_box_mirror(DevProblem d) {
+  const int64_t row = blockIdx.x * (int64_t)kTileRows + threadIdx.x;
+  const int32_t rb = d.row_box[row];
+  if (rb >= 0) d.ub[rb] = d.x[row];
 }
 
 // y32 = A32 x32 (FP32 values) on every tile: the mixed inner operator.
@@ -716,16 +729,29 @@ __global__ void k_face_correct(DevProblem d, const double* __restrict__ x, doubl
 
 // Stop test: y = A u (from the CG start) becomes K ubar = A u - T u +
 // K (ubar - u); ubar - u vanishes off the interface rows, so only the
-// interface-column layer of K is applied (w = ubar on every copy, x = u).
-__global__ void k_stop_layer(DevProblem d) {
-  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (k >= d.n_lrow) return;
+// interface-column layer of K is applied (w = ubar on every copy, x = u), and
+// on interface rows the transmission part T u (face mass and face stiffness
+// terms, the same entries as k_face_correct) is taken off.  Eight threads per
+// row, each taking every eighth entry, so that a row's entries are read as
+// contiguous runs; their sums are added in a fixed shuffle order.
+constexpr int kLayerLanes = 8;
+__global__ void __launch_bounds__(256) k_stop_layer(DevProblem d) {
+  const int64_t k = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / kLayerLanes;
+  const int sub = threadIdx.x & (kLayerLanes - 1);
   double acc = 0.0;
-  for (int32_t e = d.li_ptr[k]; e < d.li_ptr[k + 1]; ++e) {
-    const int32_t c = d.li_col[e];
-    acc = fma(d.li_val[e], d.w[c] - d.x[c], acc);
+  if (k < d.n_lrow) {
+    for (int32_t e = d.li_ptr[k] + sub; e < d.li_ptr[k + 1]; e += kLayerLanes) {
+      const int32_t c = d.li_col[e];
+      acc = fma(d.li_val[e], d.w[c] - d.x[c], acc);
+    }
+    const int32_t ir = d.li_irow[k];
+    if (ir >= 0)
+      for (int32_t e = d.im_ptr[ir] + sub; e < d.im_ptr[ir + 1]; e += kLayerLanes)
+        acc = fma(-d.im_t[e], d.x[d.im_col[e]], acc);
   }
-  d.y[d.li_row[k]] += acc;
+#pragma unroll
+  for (int o = kLayerLanes / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (k < d.n_lrow && sub == 0) d.y[d.li_row[k]] += acc;
 }
 
 // Stop test, step 2: r = sum_copies f - sum_copies K_i ubar per node, and
@@ -918,12 +944,6 @@ cudaError_t launch_profile_state(const DevProblem& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_init_mixed(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
-  OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_cg_init_mixed, s, d);
-  k_fin_init<<<fin_blocks(d), kTileRows, 0, s>>>(d, 1, cond, use_cond);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_mixed_correct(const DevProblem& d, cudaStream_t s) {
   k_mixed_correct<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d);
   return cudaGetLastError();
@@ -954,16 +974,13 @@ cudaError_t launch_spmv_plain(const DevProblem& d, const double* x, double* y, c
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
-  k_average<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
-  OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_spmv_plain, s, d, d.w, d.y);
-  if (d.n_irow) k_face_correct<<<blocks_for(d.n_irow, 256), 256, 0, s>>>(d, d.w, d.y);
-  k_residual<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
-  k_residual_fin<<<1, kResFinThreads, 0, s>>>(d, cond, use_cond);
+cudaError_t launch_box_mirror(const DevProblem& d, cudaStream_t s) {
+  k_box_mirror<<<(unsigned)d.n_tiles, kTileRows, 0, s>>>(d);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cg_start(const DevProblem& d, cudaStream_t s, int mixed) {
+  if (mixed && d.t64i) return launch_tensor_init64(d, s);
   if (mixed) OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_cg_init_mixed, s, d);
   else OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_cg_init, s, d);
   return cudaGetLastError();
@@ -977,8 +994,7 @@ cudaError_t launch_fin_init(const DevProblem& d, cudaStream_t s, unsigned long l
 
 cudaError_t launch_stop_test(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
   k_average<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
-  if (d.n_irow) k_face_correct<<<blocks_for(d.n_irow, 256), 256, 0, s>>>(d, d.x, d.y);
-  if (d.n_lrow) k_stop_layer<<<blocks_for(d.n_lrow, 256), 256, 0, s>>>(d);
+  if (d.n_lrow) k_stop_layer<<<blocks_for((int64_t)d.n_lrow * kLayerLanes, 256), 256, 0, s>>>(d);
   k_residual<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
   k_residual_fin<<<1, kResFinThreads, 0, s>>>(d, cond, use_cond);
   return cudaGetLastError();

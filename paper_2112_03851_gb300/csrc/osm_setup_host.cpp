@@ -548,6 +548,20 @@ std::string build_host_problem(const osm_mesh& mesh, const double* drho, const o
     }
   }
 
+  // interface-row index of every layer row (every interface row is a layer
+  // row: its own diagonal column is an interface column)
+  {
+    std::vector<int32_t> row_ir(hp.vec_rows, -1);
+    for (size_t q = 0; q < hp.irow.size(); ++q) row_ir[hp.irow[q]] = (int32_t)q;
+    hp.li_irow.resize(hp.li_row.size());
+    size_t covered = 0;
+    for (size_t k = 0; k < hp.li_row.size(); ++k) {
+      hp.li_irow[k] = row_ir[hp.li_row[k]];
+      covered += hp.li_irow[k] >= 0;
+    }
+    if (covered != hp.irow.size()) return "internal error: an interface row is missing from the layer";
+  }
+
   // ---- load
   build_load(hp, drho, hp.f);
   single_instance_tables(hp);
@@ -612,9 +626,13 @@ void build_box_layout(HostProblem& hp, int zchunk) {
   hp.box_tiles = tiles;
   box_cta_tables(hp, zchunk);
   hp.row_box.assign(hp.vec_rows, -1);
+  hp.box_vec.assign(hp.box_rows, -1);
   for (int64_t r = 0; r < hp.vec_rows; ++r) {
     const int32_t b = hp.row_boxidx[r];
-    if (b >= 0) hp.row_box[r] = (int32_t)(hp.box_voff[hp.tile_sub[r / kTileRows]] + b);
+    if (b >= 0) {
+      hp.row_box[r] = (int32_t)(hp.box_voff[hp.tile_sub[r / kTileRows]] + b);
+      hp.box_vec[hp.row_box[r]] = (int32_t)r;
+    }
   }
 }
 
@@ -729,6 +747,8 @@ std::string merge_problems(std::vector<HostProblem>& parts, HostProblem& out) {
     append_shift(o.li_col, p.li_col, (int32_t)vec_off);
     append(o.li_val, p.li_val);
     for (size_t k = 1; k < p.li_ptr.size(); ++k) o.li_ptr.push_back((int32_t)(p.li_ptr[k] + li_off));
+    const int32_t irow_off = (int32_t)(o.irow.size() - p.irow.size());   // o.irow already holds this part's rows
+    for (int32_t v : p.li_irow) o.li_irow.push_back(v < 0 ? -1 : v + irow_off);
     append_shift(o.cp_idx, p.cp_idx, (int32_t)vec_off);
     for (int s = 0; s < p.nsub; ++s) o.sub_inst.push_back(i);
     add_rblocks(o, i, node_off, node_off + p.n_nodes);

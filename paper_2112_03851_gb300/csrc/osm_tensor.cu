@@ -42,7 +42,7 @@ constexpr int kTxStages = 4;                     // input planes in flight
 constexpr int kTxRowsP = 640;                    // >= (256 / nx + 2) (nx + 4) for 3 <= nx <= 128
 constexpr int kTxMaxZ = 128;                     // output planes per CTA (z chunks are at most this long)
 
-// FP32 bands of every subdomain: the mass as it is, the stiffness with the
+// FP32 (and FP64) bands of every subdomain: the mass as it is, the stiffness with the
 // transmission term p of each interface side added at that side's end node
 // (a subdomain uses p_lo on the faces where it is the lower side -- its +x,
 // +y, +z sides -- and p_hi on its -x, -y, -z sides).  One block per subdomain.
@@ -66,47 +66,84 @@ __global__ void k_tensor_coef(DevProblem d) {
     }
     d.cK32[b0 + t] = (float)kv;
     d.cM32[b0 + t] = (float)mv;
+    if (d.cK64) {
+      d.cK64[b0 + t] = kv;
+      d.cM64[b0 + t] = mv;
+    }
   }
 }
 
-// Asynchronous 4-byte global -> shared copy (LDGSTS); src_bytes = 0 fills
-// the destination with zero (halo rows outside the box).
-__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+// Asynchronous 4- or 8-byte global -> shared copy (LDGSTS); src_bytes = 0
+// fills the destination with zero (halo rows outside the box).
+template <class T>
+__device__ __forceinline__ void cp_async(T* dst, const T* src, bool valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  const int n = valid ? 4 : 0;
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  const int n = valid ? (int)sizeof(T) : 0;
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// MODE 0: one step of the FP32 inner CG (the tensor counterpart of
+// Modes of the tensor kernel.
+constexpr int kTxCgStep = 0;   // FP32: one step of the inner CG (t = A z and the direction epilogue)
+constexpr int kTxApply = 1;    // FP32: y = A x
+constexpr int kTxInit = 2;     // FP64: the refinement's defect d = b - A u and the FP32 CG start
+
+// Dynamic shared memory of the tensor kernel (element type T): the staged
+// input planes, the old p and q (CG step), the two y-pass rows, the y and z
+// bands, and the block reduction.
+template <class T, int MODE>
+struct TxSmem {
+  static constexpr size_t S = 0;
+  static constexpr size_t PQ = S + sizeof(T) * kTxStages * kTxPlane;
+  static constexpr size_t TM = PQ + (MODE == kTxCgStep ? sizeof(float) * kTxStages * 2 * kTileRows : 0);
+  static constexpr size_t TK = TM + sizeof(T) * kTxRowsP;
+  static constexpr size_t CY = TK + sizeof(T) * kTxRowsP;
+  static constexpr size_t CZ = CY + sizeof(T) * kTxMaxRows * 10;
+  static constexpr size_t RED = (CZ + sizeof(T) * kTxMaxZ * 10 + 15) / 16 * 16;
+  static constexpr size_t BYTES = RED + sizeof(double) * 3 * kTileSlices + 16;
+};
+
+// kTxCgStep: one step of the FP32 inner CG (the tensor counterpart of
 // k_cg_spmv_dir32): t = A z, then p = z + beta p, q = t + beta q (first step
 // beta = 0: p = z, q = t) and the CTA's partial of p.q (scaled FP32 dots as in
 // the SELL kernel) into part0[cta]; the subdomain's last CTA (a ticket, no
 // waiting) adds the partials in a fixed order and stores p.q and alpha = r.z
-// / p.q for the update kernel.  MODE 1: y = A x (x, y in the box layout).
+// / p.q for the update kernel.
+// kTxApply: y = A x (x, y in the box layout).
+// kTxInit (T = double): the mixed form's refinement step starts here when
+// the tensor form is in use: with u in the box layout (ub), t = A u in FP64,
+// and for every unknown (vector row `row`) y[row] = t, the defect d = b - t,
+// r = d and z = D^-1 r in FP32 for the inner CG (x = 0), and the CTA's
+// partials of ||d||^2, ||b||^2 and r.z (k_fin_init adds them).
 // A CTA covers 256 (x, y) columns of one box and one chunk of its z range
 // (box_dims: the chunk length and the number of column blocks), marching
 // over the chunk's planes and the two halo planes on either side.  The input
 // planes stream through kTxStages shared-memory stages filled by
 // asynchronous copies issued kTxStages - 1 planes ahead, together with the
-// old p and q of the output plane they complete.  The plane loop is unrolled
-// by five, so the five-plane rings of the partial products live in fixed
-// registers.
-template <int MODE>
-__global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const float* __restrict__ xin,
-                                                           float* __restrict__ yout) {
-  __shared__ __align__(16) float S[kTxStages][kTxPlane];
-  __shared__ float PQ[MODE == 0 ? kTxStages : 1][2][MODE == 0 ? kTileRows : 1];   // old p, q of an output plane
-  __shared__ float TM[kTxRowsP], TK[kTxRowsP];   // y-pass rows, two zero columns either side
-  __shared__ float CY[kTxMaxRows][10];           // y bands of the CTA's rows: M then K~
-  __shared__ float CZ[kTxMaxZ][10];              // z bands of the chunk's output planes
-  __shared__ double red[kTileSlices];
-  __shared__ bool s_last;
+// old p and q of the output plane they complete (CG step).  The plane loop is
+// unrolled by five, so the five-plane rings of the partial products live in
+// fixed registers.
+template <class T, int MODE>
+__global__ void __launch_bounds__(kTileRows, sizeof(T) == 4 ? 3 : 2)
+    k_tensor(DevProblem d, const T* __restrict__ xin, T* __restrict__ yout) {
+  using L = TxSmem<T, MODE>;
+  extern __shared__ __align__(16) unsigned char smem[];
+  T (*S)[kTxPlane] = reinterpret_cast<T (*)[kTxPlane]>(smem + L::S);
+  float (*PQ)[2][kTileRows] = reinterpret_cast<float (*)[2][kTileRows]>(smem + L::PQ);
+  T* TM = reinterpret_cast<T*>(smem + L::TM);   // y-pass rows, two zero columns either side
+  T* TK = reinterpret_cast<T*>(smem + L::TK);
+  T (*CY)[10] = reinterpret_cast<T (*)[10]>(smem + L::CY);   // y bands of the CTA's rows: M then K~
+  T (*CZ)[10] = reinterpret_cast<T (*)[10]>(smem + L::CZ);   // z bands of the chunk's output planes
+  double (*red)[kTileSlices] = reinterpret_cast<double (*)[kTileSlices]>(smem + L::RED);
+  bool* s_last = reinterpret_cast<bool*>(smem + L::RED + sizeof(double) * 3 * kTileSlices);
   const int cta = blockIdx.x;
   const int s = d.cta_sub[cta];
-  if (MODE == 0 && !d.st.active[s]) return;
+  if (MODE == kTxCgStep && !d.st.active[s]) return;
   const int* dims = d.box_dims + kBoxDims * s;
   const int nx = dims[0], ny = dims[1], nz = dims[2], fm = dims[3], zc = dims[4], ncb = dims[5];
   const int nxy = nx * ny, nxp = nx + 4;
@@ -120,8 +157,15 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
   const int nrow = jhi - jlo + 1, nload = (nrow + 4) * nx, ntr = nrow * nx;
   const int j = valid ? col / nx : jlo, i = valid ? col - j * nx : 0;
   const int64_t bx = (int64_t)d.box_band0[s] * 5, by = bx + 5 * (int64_t)nx, bz = by + 5 * (int64_t)ny;
-  const float* __restrict__ cK = d.cK32;
-  const float* __restrict__ cM = d.cM32;
+  const T* __restrict__ cK;
+  const T* __restrict__ cM;
+  if constexpr (sizeof(T) == 4) {
+    cK = d.cK32;
+    cM = d.cM32;
+  } else {
+    cK = d.cK64;
+    cM = d.cM64;
+  }
   for (int t = threadIdx.x; t < 5 * nrow; t += kTileRows) {
     CY[t / 5][t % 5] = cM[by + 5 * (int64_t)jlo + t];
     CY[t / 5][5 + t % 5] = cK[by + 5 * (int64_t)jlo + t];
@@ -133,10 +177,10 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
   for (int t = threadIdx.x; t < 4 * nrow; t += kTileRows) {   // the zero columns of TM, TK
     const int r = t >> 2, c = t & 3;
     const int at = r * nxp + (c < 2 ? c : nx + c);
-    TM[at] = 0.f;
-    TK[at] = 0.f;
+    TM[at] = T(0);
+    TK[at] = T(0);
   }
-  float kx[5], mx[5];
+  T kx[5], mx[5];
 #pragma unroll
   for (int a = 0; a < 5; ++a) {
     kx[a] = cK[bx + 5 * i + a];
@@ -165,12 +209,15 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
     yrow[m] = idx < ntr ? idx / nx : -1;
     ypad[m] = yrow[m] >= 0 ? yrow[m] * nxp + 2 + (idx - yrow[m] * nx) : 0;
   }
-  const int xbase = (j - jlo) * nxp + i;   // TM index of this column's neighbour i - 2
+  const int xbase = (j - jlo) * nxp + i;    // TM index of this column's neighbour i - 2
   const int zown = (j - jlo + 2) * nx + i;  // this column in the staged plane
-  const float* __restrict__ src = MODE == 0 ? d.z32 : xin;
+  const T* __restrict__ src;
+  if constexpr (MODE == kTxCgStep) src = d.z32;
+  else if constexpr (MODE == kTxInit) src = d.ub;
+  else src = xin;
   float beta = 0.f, sc = 1.f;
   bool first = true;
-  if (MODE == 0) {
+  if (MODE == kTxCgStep) {
     const double b64 = d.st.beta[s];
     first = b64 == 0.0;
     beta = (float)b64;
@@ -182,22 +229,23 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
   // stays uniform
   auto issue = [&](int kk, int st) {
     if (kk >= 0 && kk < nz) {
-      const float* pl = src + voff + (int64_t)nxy * kk;
+      const T* pl = src + voff + (int64_t)nxy * kk;
 #pragma unroll
       for (int m = 0; m < kTxPre; ++m)
-        if (goff[m] >= -1) cp_async4(&S[st][threadIdx.x + m * kTileRows], pl + max(goff[m], 0), goff[m] >= 0);
+        if (goff[m] >= -1) cp_async(&S[st][threadIdx.x + m * kTileRows], pl + max(goff[m], 0), goff[m] >= 0);
     }
-    if (MODE == 0 && !first && valid && kk - 2 >= k0 && kk - 2 < k1) {
+    if (MODE == kTxCgStep && !first && valid && kk - 2 >= k0 && kk - 2 < k1) {
       const int64_t row = voff + col + (int64_t)nxy * (kk - 2);
-      cp_async4(&PQ[st][0][threadIdx.x], d.p32 + row, true);
-      cp_async4(&PQ[st][1][threadIdx.x], d.q32 + row, true);
+      cp_async(&PQ[st][0][threadIdx.x], d.p32 + row, true);
+      cp_async(&PQ[st][1][threadIdx.x], d.q32 + row, true);
     }
     cp_async_commit();
   };
-  float ph[5], qh[5], zh[5];
+  T ph[5], qh[5], zh[5];
 #pragma unroll
-  for (int c = 0; c < 5; ++c) { ph[c] = 0.f; qh[c] = 0.f; zh[c] = 0.f; }
-  float vv = 0.f;
+  for (int c = 0; c < 5; ++c) { ph[c] = T(0); qh[c] = T(0); zh[c] = T(0); }
+  float vv = 0.f;                    // CG step: p.q
+  double v0 = 0.0, v1 = 0.0, v2 = 0.0;   // init: ||d||^2, ||b||^2, r.z
 #pragma unroll
   for (int st = 0; st < kTxStages - 1; ++st) issue(k0 - 2 + st, st);
   int st = 0;
@@ -211,36 +259,36 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
         cp_async_wait<kTxStages - 1>();   // this thread's copies of plane kk have landed
         __syncthreads();                  // ... and every other thread's
         const bool pin = kk >= 0 && kk < nz;
-        float zc_own = 0.f;
+        T zc_own = T(0);
         if (pin) {
           // y pass: My z and K~y z on the CTA's rows, every x
 #pragma unroll
           for (int m = 0; m < kTxY; ++m) {
             if (yrow[m] >= 0) {
               const int idx = (int)threadIdx.x + m * kTileRows;
-              const float* cy = CY[yrow[m]];
-              float sm = 0.f, sk = 0.f;
+              const T* cy = CY[yrow[m]];
+              T sm = T(0), sk = T(0);
 #pragma unroll
               for (int b = 0; b < 5; ++b) {
-                const float v = S[st][idx + b * nx];
-                sm = fmaf(cy[b], v, sm);
-                sk = fmaf(cy[5 + b], v, sk);
+                const T v = S[st][idx + b * nx];
+                sm = fma(cy[b], v, sm);
+                sk = fma(cy[5 + b], v, sk);
               }
               TM[ypad[m]] = sm;
               TK[ypad[m]] = sk;
             }
           }
-          if (valid) zc_own = S[st][zown];
+          if (MODE == kTxCgStep && valid) zc_own = S[st][zown];
         }
         __syncthreads();   // TM, TK complete; stage st is free for the next issue
         // x pass for this thread's column: P = K~x (My z) + Mx (K~y z), Q = Mx (My z)
-        float P = 0.f, Q = 0.f;
+        T P = T(0), Q = T(0);
         if (pin && valid) {
 #pragma unroll
           for (int a = 0; a < 5; ++a) {
-            const float tm = TM[xbase + a], tk = TK[xbase + a];
-            P = fmaf(kx[a], tm, fmaf(mx[a], tk, P));
-            Q = fmaf(mx[a], tm, Q);
+            const T tm = TM[xbase + a], tk = TK[xbase + a];
+            P = fma(kx[a], tm, fma(mx[a], tk, P));
+            Q = fma(mx[a], tm, Q);
           }
         }
         // ring slot u holds plane kk; slot (u + 1 + c) % 5 holds plane kk - 4 + c
@@ -249,13 +297,14 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
         zh[u] = zc_own;
         const int k = kk - 2;   // output plane: its neighbours k-2 .. k+2 are in the rings
         if (k >= k0 && valid) {
-          const float* cz = CZ[k - k0];
-          float t = 0.f;
+          const T* cz = CZ[k - k0];
+          T t = T(0);
 #pragma unroll
-          for (int c = 0; c < 5; ++c) t = fmaf(cz[c], ph[(u + 1 + c) % 5], fmaf(cz[5 + c], qh[(u + 1 + c) % 5], t));
-          if (dcol || ((fm & 16) && k == 0) || ((fm & 32) && k == nz - 1)) t = 0.f;
+          for (int c = 0; c < 5; ++c) t = fma(cz[c], ph[(u + 1 + c) % 5], fma(cz[5 + c], qh[(u + 1 + c) % 5], t));
+          const bool dir = dcol || ((fm & 16) && k == 0) || ((fm & 32) && k == nz - 1);
           const int64_t row = voff + col + (int64_t)nxy * k;
-          if (MODE == 0) {
+          if constexpr (MODE == kTxCgStep) {
+            if (dir) t = 0.f;
             const float z = zh[(u + 3) % 5];
             float p = z, q = t;
             if (!first) {   // this thread's own staged values: no barrier needed
@@ -265,8 +314,23 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
             d.p32[row] = p;
             d.q32[row] = q;
             vv = fmaf(p * sc, q * sc, vv);
+          } else if constexpr (MODE == kTxInit) {
+            const int32_t vr = d.box_vec[row];   // the unknown's vector row (-1: Dirichlet)
+            if (!dir && vr >= 0) {
+              const double b = d.b[vr];
+              const double dfc = b - t;
+              d.y[vr] = t;
+              const float r = (float)dfc;
+              const float z = d.dinv32b[row] * r;
+              d.r32[row] = r;
+              d.z32[row] = z;   // p = z is formed by the first CG-step kernel (beta = 0)
+              d.x32[row] = 0.f;
+              v0 = fma(dfc, dfc, v0);
+              v1 = fma(b, b, v1);
+              v2 += (double)r * (double)z;
+            }
           } else {
-            yout[row] = t;
+            yout[row] = dir ? T(0) : t;
           }
         }
         st = st + 1 == kTxStages ? 0 : st + 1;
@@ -274,26 +338,26 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
     }
   }
   cp_async_wait<0>();   // no copy outlives the CTA
-  if (MODE == 0) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if constexpr (MODE == kTxCgStep) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) vv += __shfl_xor_sync(0xffffffffu, vv, o);
-    if (lane == 0) red[warp] = (double)vv * d.st.isc2[s];
+    if (lane == 0) red[0][warp] = (double)vv * d.st.isc2[s];
     __syncthreads();
     if (threadIdx.x == 0) {
       double acc = 0.0;
 #pragma unroll
-      for (int w = 0; w < kTileSlices; ++w) acc += red[w];
+      for (int w = 0; w < kTileSlices; ++w) acc += red[0][w];
       d.part0[cta] = acc;
       // the subdomain's last CTA forms p.q and alpha (a ticket, not a wait)
       __threadfence();
       const unsigned nct = (unsigned)(d.sub_cta0[s + 1] - d.sub_cta0[s]);
-      const unsigned t = atomicAdd(&d.st.tcnt[s], 1u);
-      s_last = t == nct - 1u;
-      if (s_last) d.st.tcnt[s] = 0u;
+      const unsigned tk = atomicAdd(&d.st.tcnt[s], 1u);
+      *s_last = tk == nct - 1u;
+      if (*s_last) d.st.tcnt[s] = 0u;
     }
     __syncthreads();
-    if (s_last && warp == 0) {
+    if (*s_last && warp == 0) {
       __threadfence();
       const int64_t a0 = d.sub_cta0[s];
       const double pq = warp_sum_parts(d.part0, a0, d.sub_cta0[s + 1] - a0);
@@ -301,6 +365,22 @@ __global__ void __launch_bounds__(kTileRows, 3) k_tensor32(DevProblem d, const f
         d.st.pq[s] = pq;
         d.st.alpha[s] = (pq > 0.0 && isfinite(pq)) ? d.st.rho[s] / pq : 0.0;
       }
+    }
+  } else if constexpr (MODE == kTxInit) {
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    v2 = warp_sum(v2);
+    if (lane == 0) {
+      red[0][warp] = v0;
+      red[1][warp] = v1;
+      red[2][warp] = v2;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+      double acc = 0.0;
+#pragma unroll
+      for (int w = 0; w < kTileSlices; ++w) acc += red[threadIdx.x][w];
+      (threadIdx.x == 0 ? d.part0 : threadIdx.x == 1 ? d.part1 : d.part2)[cta] = acc;
     }
   }
 }
@@ -327,13 +407,32 @@ cudaError_t launch_tensor_coef(const DevProblem& d, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t tensor_kernel_setup() {
+  cudaError_t e = cudaFuncSetAttribute(k_tensor<float, kTxCgStep>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)TxSmem<float, kTxCgStep>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tensor<float, kTxApply>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TxSmem<float, kTxApply>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tensor<double, kTxInit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TxSmem<double, kTxInit>::BYTES);
+  return e;
+}
+
 cudaError_t launch_tensor_dir32(const DevProblem& d, cudaStream_t s) {
-  k_tensor32<0><<<(unsigned)d.n_cta32, kTileRows, 0, s>>>(d, nullptr, nullptr);
+  k_tensor<float, kTxCgStep><<<(unsigned)d.n_cta32, kTileRows, TxSmem<float, kTxCgStep>::BYTES, s>>>(d, nullptr,
+                                                                                                    nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_tensor_apply32(const DevProblem& d, const float* x, float* y, cudaStream_t s) {
-  k_tensor32<1><<<(unsigned)d.n_cta32, kTileRows, 0, s>>>(d, x, y);
+  k_tensor<float, kTxApply><<<(unsigned)d.n_cta32, kTileRows, TxSmem<float, kTxApply>::BYTES, s>>>(d, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tensor_init64(const DevProblem& d, cudaStream_t s) {
+  k_tensor<double, kTxInit><<<(unsigned)d.n_cta32, kTileRows, TxSmem<double, kTxInit>::BYTES, s>>>(d, nullptr,
+                                                                                                  nullptr);
   return cudaGetLastError();
 }
 

@@ -29,12 +29,12 @@ def _instances():
     return [a, b, c, d]
 
 
-@pytest.mark.parametrize("prec, fp32_op", [("fp64", 0), ("mixed", 1), ("mixed", 2)])
-def test_batch_equals_single_solves(osm, prec, fp32_op):
+@pytest.mark.parametrize("prec, fp32_op, start", [("fp64", 0, 0), ("mixed", 1, 0), ("mixed", 2, 1), ("mixed", 2, 2)])
+def test_batch_equals_single_solves(osm, prec, fp32_op, start):
     probs = _instances()
-    # the FP32 operator is pinned (SELL or tensor form): the autotuner could
-    # pick differently for the batch and for a single instance
-    kw = dict(prec=prec, inner_rtol=1e-13, max_outer=3000, fp32_operator=fp32_op)
+    # the FP32 operator and the refinement's FP64 start are pinned: the
+    # autotuner could pick differently for the batch and for a single instance
+    kw = dict(prec=prec, inner_rtol=1e-13, max_outer=3000, fp32_operator=fp32_op, fp64_start=start)
     bs = osm.BatchSolver(probs, **kw)
     phi, iters, rel = bs.solve(rtol=1e-10)
     assert np.all(rel <= 1e-10)

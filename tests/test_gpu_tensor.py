@@ -120,18 +120,23 @@ def _mono(prob):
 
 @pytest.mark.parametrize("case", ["sphere16", "uneven"])
 def test_tensor_mixed_solve_matches_oracle_and_sell(osm, case):
+    """Mixed solves on the SELL FP32 matrix, on the tensor form with the
+    SELL FP64 defect, and on the tensor form with the FP64 tensor defect
+    (u mirrored in the box layout) all reach the oracle's solution."""
     prob = gen.sphere_problem(16, 2, 10.0) if case == "sphere16" else small_uneven()
     ref = _mono(prob)
     phis = {}
-    for op in (1, 2):
+    for op, start in ((1, 0), (2, 1), (2, 2)):
         sol = osm.Solver.from_problem(prob, prec="mixed", mixed_inner_rtol=0.3, inner_rtol=1e-13, max_outer=4000,
-                                      fp32_operator=op)
+                                      fp32_operator=op, fp64_start=start)
         assert sol.info["fp32_operator"] == op
+        assert sol.info["fp64_start"] == (start if op == 2 else 1)
         phi, n, rel = sol.solve(rtol=1e-10)
         assert rel <= 1e-10
-        phis[op] = phi.cpu().numpy()
-        assert np.linalg.norm(phis[op] - ref) <= 1e-8 * np.linalg.norm(ref), op
-    assert np.linalg.norm(phis[1] - phis[2]) <= 1e-8 * np.linalg.norm(ref)
+        phis[(op, start)] = phi.cpu().numpy()
+        assert np.linalg.norm(phis[(op, start)] - ref) <= 1e-8 * np.linalg.norm(ref), (op, start)
+    for key in ((2, 1), (2, 2)):
+        assert np.linalg.norm(phis[(1, 0)] - phis[key]) <= 1e-8 * np.linalg.norm(ref), key
 
 
 def test_second_order_condition_falls_back_to_sell(osm):
@@ -157,9 +162,9 @@ def test_second_order_condition_falls_back_to_sell(osm):
 
 def test_tensor_batch_equals_single_solves(osm):
     probs = [gen.sphere_problem(8, 2, 4.0), small_uneven(), gen.sphere_problem(6, 1, 3.0)]
-    kw = dict(prec="mixed", inner_rtol=1e-13, max_outer=3000, fp32_operator=2, mixed_inner_rtol=0.3)
+    kw = dict(prec="mixed", inner_rtol=1e-13, max_outer=3000, fp32_operator=2, fp64_start=2, mixed_inner_rtol=0.3)
     bs = osm.BatchSolver(probs, **kw)
-    assert bs.info["fp32_operator"] == 2
+    assert bs.info["fp32_operator"] == 2 and bs.info["fp64_start"] == 2
     phi, iters, rel = bs.solve(rtol=1e-10)
     assert np.all(rel <= 1e-10)
     for i, q in enumerate(probs):
