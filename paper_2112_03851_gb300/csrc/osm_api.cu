@@ -309,6 +309,8 @@ osm_status upload_problem(osm_ctx* h) {
       d.box_vec = box_vec;
       OSM_CUDA(h, dalloc(h, &d.ub, hp.box_rows));
       OSM_CUDA(h, dalloc(h, &d.cK64, hp.band_k.size()));
+      OSM_CUDA(h, dalloc(h, &d.cKp32, hp.band_k.size()));
+      OSM_CUDA(h, dalloc(h, &d.dl32, hp.box_rows));
       OSM_CUDA(h, dalloc(h, &d.cM64, hp.band_m.size()));
       OSM_CUDA(h, tensor_kernel_setup());
       std::vector<float> dib(hp.box_rows, 0.f);
@@ -1278,10 +1280,12 @@ osm_status osm_stats(osm_handle h, osm_stats_t* o) {
     // solve: once the nodal load, the first RHS gather and CG start; per
     // Schwarz iteration the CG finaliser, FP64 correction (mixed), exchange
     // (if any face), the next RHS gather and CG start, average, interface
-    // layer (if any), residual partials, residual finaliser; per CG step SpMV
-    // (+ direction epilogue in FP32) and update (+ the step's finish), plus
-    // the FP64 direction
-    const int64_t per_outer = 1 + mixed + faces + 2 + 1 + (h->hp.li_row.empty() ? 0 : 1) + 2;
+    // layer (if any; on the tensor form the transmission correction and the
+    // FP32 tensor kernel), residual partials, residual finaliser; per CG step
+    // SpMV (+ direction epilogue in FP32) and update (+ the step's finish),
+    // plus the FP64 direction
+    const int64_t layer = h->d.dl32 ? 1 + (h->hp.irow.empty() ? 0 : 1) : (h->hp.li_row.empty() ? 0 : 1);
+    const int64_t per_outer = 1 + mixed + faces + 2 + 1 + layer + 2;
     o->n_launches = 3 + per_outer * c.n_outer + (mixed ? 2 : 3) * (int64_t)c.total_inner;
   }
   o->relres = c.relres;

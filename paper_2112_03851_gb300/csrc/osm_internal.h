@@ -320,6 +320,9 @@ struct DevProblem {
   double* ub;
   const int32_t* box_vec;
   double *cK64, *cM64;
+  // stop test on the tensor form (handles with a box layout): ubar - u in the
+  // box layout (FP32, written by k_average) and the plain FP32 stiffness bands
+  float *dl32, *cKp32;
   // partial range table of the CG start's ||r||^2, ||b||^2, r.z partials
   // (sub_tile0 for the SELL kernels, sub_cta0 for the tensor start)
   const int64_t* sub_init0;
@@ -409,6 +412,7 @@ cudaError_t launch_tensor_dir32(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_tensor_apply32(const DevProblem& d, const float* x, float* y, cudaStream_t s);
 cudaError_t launch_tensor_init64(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_box_mirror(const DevProblem& d, cudaStream_t s);
+cudaError_t launch_tensor_layer(const DevProblem& d, cudaStream_t s);
 // Shared-memory limits of the tensor kernels (once per process and device).
 cudaError_t tensor_kernel_setup();
 // The DevProblem seen by the FP32 CG kernels: the box layout's tile tables

@@ -700,7 +700,11 @@ __global__ void k_average(DevProblem d) {
     for (int32_t c = c0; c < c1; ++c) s += d.x[d.cp_idx[c]];
     const double ub = copy_mean(s, c1 - c0);
     d.phi[n] = ub;
-    for (int32_t c = c0; c < c1; ++c) d.w[d.cp_idx[c]] = ub;
+    for (int32_t c = c0; c < c1; ++c) {
+      const int32_t r = d.cp_idx[c];
+      d.w[r] = ub;
+      if (d.dl32) d.dl32[d.row_box[r]] = (float)(ub - d.x[r]);   // ubar - u for the tensor layer
+    }
   }
 }
 
@@ -994,7 +998,13 @@ cudaError_t launch_fin_init(const DevProblem& d, cudaStream_t s, unsigned long l
 
 cudaError_t launch_stop_test(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
   k_average<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
-  if (d.n_lrow) k_stop_layer<<<blocks_for((int64_t)d.n_lrow * kLayerLanes, 256), 256, 0, s>>>(d);
+  if (d.dl32) {   // box layout: the transmission part in FP64, K (ubar - u) by the FP32 tensor kernel
+    if (d.n_irow) k_face_correct<<<blocks_for(d.n_irow, 256), 256, 0, s>>>(d, d.x, d.y);
+    cudaError_t e = launch_tensor_layer(d, s);
+    if (e != cudaSuccess) return e;
+  } else if (d.n_lrow) {
+    k_stop_layer<<<blocks_for((int64_t)d.n_lrow * kLayerLanes, 256), 256, 0, s>>>(d);
+  }
   k_residual<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
   k_residual_fin<<<1, kResFinThreads, 0, s>>>(d, cond, use_cond);
   return cudaGetLastError();

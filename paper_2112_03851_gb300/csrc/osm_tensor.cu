@@ -66,6 +66,7 @@ __global__ void k_tensor_coef(DevProblem d) {
     }
     d.cK32[b0 + t] = (float)kv;
     d.cM32[b0 + t] = (float)mv;
+    d.cKp32[b0 + t] = (float)d.band_k[b0 + t];   // plain stiffness (stop-test layer)
     if (d.cK64) {
       d.cK64[b0 + t] = kv;
       d.cM64[b0 + t] = mv;
@@ -92,6 +93,7 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 constexpr int kTxCgStep = 0;   // FP32: one step of the inner CG (t = A z and the direction epilogue)
 constexpr int kTxApply = 1;    // FP32: y = A x
 constexpr int kTxInit = 2;     // FP64: the refinement's defect d = b - A u and the FP32 CG start
+constexpr int kTxLayer = 3;    // FP32: y += K (ubar - u) for the stop test (plain stiffness K)
 
 // Dynamic shared memory of the tensor kernel (element type T): the staged
 // input planes, the old p and q (CG step), the two y-pass rows, the y and z
@@ -115,6 +117,12 @@ struct TxSmem {
 // waiting) adds the partials in a fixed order and stores p.q and alpha = r.z
 // / p.q for the update kernel.
 // kTxApply: y = A x (x, y in the box layout).
+// kTxLayer: the stop test's interface correction.  The difference of the
+// averaged and the local iterate, ubar - u, is nonzero on interface nodes
+// only and small; K (ubar - u) with the plain stiffness K (no transmission
+// term) in FP32 is added to y = A u - T u (FP64, vector rows) to give K ubar.
+// Its FP32 rounding, ~1e-7 of |K| |ubar - u|, is far below the residual it
+// enters.
 // kTxInit (T = double): the mixed form's refinement step starts here when
 // the tensor form is in use: with u in the box layout (ub), t = A u in FP64,
 // and for every unknown (vector row `row`) y[row] = t, the defect d = b - t,
@@ -159,7 +167,10 @@ __global__ void __launch_bounds__(kTileRows, sizeof(T) == 4 ? 3 : 2)
   const int64_t bx = (int64_t)d.box_band0[s] * 5, by = bx + 5 * (int64_t)nx, bz = by + 5 * (int64_t)ny;
   const T* __restrict__ cK;
   const T* __restrict__ cM;
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (MODE == kTxLayer) {
+    cK = d.cKp32;
+    cM = d.cM32;
+  } else if constexpr (sizeof(T) == 4) {
     cK = d.cK32;
     cM = d.cM32;
   } else {
@@ -214,6 +225,7 @@ __global__ void __launch_bounds__(kTileRows, sizeof(T) == 4 ? 3 : 2)
   const T* __restrict__ src;
   if constexpr (MODE == kTxCgStep) src = d.z32;
   else if constexpr (MODE == kTxInit) src = d.ub;
+  else if constexpr (MODE == kTxLayer) src = d.dl32;
   else src = xin;
   float beta = 0.f, sc = 1.f;
   bool first = true;
@@ -329,6 +341,9 @@ __global__ void __launch_bounds__(kTileRows, sizeof(T) == 4 ? 3 : 2)
               v1 = fma(b, b, v1);
               v2 += (double)r * (double)z;
             }
+          } else if constexpr (MODE == kTxLayer) {
+            const int32_t vr = d.box_vec[row];
+            if (!dir && vr >= 0) d.y[vr] += (double)t;
           } else {
             yout[row] = dir ? T(0) : t;
           }
@@ -416,6 +431,9 @@ cudaError_t tensor_kernel_setup() {
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tensor<double, kTxInit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TxSmem<double, kTxInit>::BYTES);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tensor<float, kTxLayer>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TxSmem<float, kTxLayer>::BYTES);
   return e;
 }
 
@@ -427,6 +445,12 @@ cudaError_t launch_tensor_dir32(const DevProblem& d, cudaStream_t s) {
 
 cudaError_t launch_tensor_apply32(const DevProblem& d, const float* x, float* y, cudaStream_t s) {
   k_tensor<float, kTxApply><<<(unsigned)d.n_cta32, kTileRows, TxSmem<float, kTxApply>::BYTES, s>>>(d, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tensor_layer(const DevProblem& d, cudaStream_t s) {
+  k_tensor<float, kTxLayer><<<(unsigned)d.n_cta32, kTileRows, TxSmem<float, kTxLayer>::BYTES, s>>>(d, nullptr,
+                                                                                                   nullptr);
   return cudaGetLastError();
 }
 
