@@ -227,6 +227,31 @@ __device__ __forceinline__ bool out_of_time(DevCtl* c) {
   return false;
 }
 
+// End of the SpMV kernel of a CG step, called by every thread after thread 0
+// wrote the block's p.q partial: the subdomain's last block (a ticket on
+// st.tcnt, no waiting) adds the subdomain's partials part0[sub_part0[s] ..
+// sub_part0[s+1]) in a fixed order and stores p.q and alpha = rho / p.q (0 on
+// a breakdown, p.q <= 0 or not finite) for the update kernel.
+__device__ __forceinline__ void cg_alpha_ticket(const DevProblem& d, int s, bool* s_last) {
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned n = (unsigned)(d.sub_part0[s + 1] - d.sub_part0[s]);
+    const unsigned t = atomicAdd(&d.st.tcnt[s], 1u);
+    *s_last = t == n - 1u;
+    if (*s_last) d.st.tcnt[s] = 0u;
+  }
+  __syncthreads();
+  if (*s_last && (threadIdx.x >> 5) == 0) {
+    __threadfence();
+    const int64_t a0 = d.sub_part0[s];
+    const double pq = warp_sum_parts(d.part0, a0, d.sub_part0[s + 1] - a0);
+    if ((threadIdx.x & 31) == 0) {
+      d.st.pq[s] = pq;
+      d.st.alpha[s] = (pq > 0.0 && isfinite(pq)) ? d.st.rho[s] / pq : 0.0;
+    }
+  }
+}
+
 // Ticket of the last block: returns true in every thread of the block that
 // finished last among `total` blocks counted on *cnt (and resets it).
 __device__ __forceinline__ bool last_block(unsigned* cnt, unsigned total, bool* flag_sm) {

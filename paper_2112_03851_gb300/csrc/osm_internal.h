@@ -292,9 +292,6 @@ struct DevProblem {
   // Range table of the p.q partials of the CG step's SpMV kernel (sub_tile0
   // for the SELL kernels; sub_cta0 for the tensor kernel).
   const int64_t* sub_part0;
-  // 1: the CG step's SpMV kernel already formed p.q and alpha per subdomain
-  // (st.pq, st.alpha); 0: the update kernel adds the p.q partials itself
-  int32_t alpha_ready;
   // FP32 inner solve on the tensor-product operator in the box layout (t32 =
   // 1; else the FP32 SELL operator in the vector-row layout).  The x32 .. q32
   // vectors then hold box rows, dinv32b is the box-layout Jacobi diagonal.

@@ -133,6 +133,7 @@ __device__ __forceinline__ void tile_dots(T (&v)[NV], double isc2, double (*sm)[
 template <class T, int RPL, bool C16>
 __global__ void __launch_bounds__(kTileRows) k_cg_spmv(DevProblem d, CgVec<T> v) {
   __shared__ double sm[1][kTileRows / RPL];
+  __shared__ bool s_last;
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
   if (!d.st.active[s]) return;
@@ -150,6 +151,7 @@ __global__ void __launch_bounds__(kTileRows) k_cg_spmv(DevProblem d, CgVec<T> v)
   double out[1] = {(double)vv[0]};
   block_sum_d<1, kTileRows / RPL>(out, sm);
   if (threadIdx.x == 0) d.part0[tile] = out[0] * (sizeof(T) == 4 ? d.st.isc2[s] : 1.0);
+  cg_alpha_ticket(d, s, &s_last);
 }
 
 // Per-subdomain finalisers: one warp per subdomain adds the subdomain's tile
@@ -212,13 +214,7 @@ __device__ __forceinline__ void cg_step_finish(DevProblem& d, const int64_t* __r
   const int64_t b0 = ub0[s], nb = ub0[s + 1] - b0;
   const double rz = warp_sum_parts(d.part1, b0, nb);
   const double rr = warp_sum_parts(d.part2, b0, nb);
-  double pq;
-  if (d.alpha_ready) {
-    pq = d.st.pq[s];
-  } else {
-    const int64_t c0 = d.sub_part0[s];
-    pq = warp_sum_parts(d.part0, c0, d.sub_part0[s + 1] - c0);
-  }
+  const double pq = d.st.pq[s];   // formed by the step's SpMV kernel (cg_alpha_ticket)
   if (lane == 0) {
     const int it = d.st.iters[s] + 1;
     d.st.iters[s] = it;
@@ -278,6 +274,7 @@ __global__ void __launch_bounds__(kTileRows) k_cg_direction(DevProblem d, CgVec<
 template <int RPL, bool C16>
 __global__ void __launch_bounds__(kTileRows) k_cg_spmv_dir32(DevProblem d) {
   __shared__ double sm[1][kTileSlices];
+  __shared__ bool s_last;
   const int64_t tile = blockIdx.x;
   const int s = d.tile_sub[tile];
   if (!d.st.active[s]) return;
@@ -304,23 +301,20 @@ __global__ void __launch_bounds__(kTileRows) k_cg_spmv_dir32(DevProblem d) {
   double out[1];
   tile_dots<float, 1, kTileSlices / RPL>(vv, d.st.isc2[s], sm, out);
   if (threadIdx.x == 0) d.part0[tile] = out[0];
+  cg_alpha_ticket(d, s, &s_last);
 }
 
-// alpha = rho / (p.q) (a breakdown, p.q <= 0, leaves the iterate alone and
-// the step's finish stops the subdomain), x += alpha p, r -= alpha q,
-// z = D^-1 r, and the block's partials of r.z and ||r||^2; the subdomain's
-// last block to finish then ends the step (cg_step_finish, cg_step_arrive).
-// A block covers up to G consecutive tiles of one subdomain (d.ub_tile0 /
-// d.ub64_tile0; FP32: 8, FP64: 2, which keeps its registers, and so its
-// occupancy, up).  Every thread first issues the loads of all its rows; then
-// every warp forms alpha itself from the subdomain's p.q partials (the same
-// expression and summation order in every warp and block, so the step is
-// bit-identical to a separate alpha kernel, with no block-wide wait for
-// it).  Each thread adds its rows' r.z and r.r in row order, the block adds
-// its threads' sums in a fixed order and writes one partial pair per block.
+// With alpha = rho / (p.q) from the step's SpMV kernel (cg_alpha_ticket; 0
+// on a breakdown, which leaves the iterate alone and makes the step's finish
+// stop the subdomain): x += alpha p, r -= alpha q, z = D^-1 r, and the
+// block's partials of r.z and ||r||^2; the subdomain's last block to finish
+// then ends the step (cg_step_finish, cg_step_arrive).  A block covers up to
+// G consecutive tiles of one subdomain (d.ub_tile0 / d.ub64_tile0; FP32: 8,
+// FP64: 2, which keeps its registers, and so its occupancy, up).  Each
+// thread adds its rows' r.z and r.r in row order, the block adds its
+// threads' sums in a fixed order and writes one partial pair per block.
 // T = double: the FP64 CG (FP64 dots, staged in shared memory: FP64 adds are
-// scarce); T = float: the mixed form's inner CG (scaled FP32 dots, FP32 warp
-// sums widened to FP64 across warps).
+// scarce); the mixed form's FP32 update is k_cg_update32.
 template <class T, int G>
 __global__ void __launch_bounds__(kTileRows) k_cg_update_a(DevProblem d, CgVec<T> v, unsigned long long cond,
                                                            int use_cond) {
@@ -350,14 +344,7 @@ __global__ void __launch_bounds__(kTileRows) k_cg_update_a(DevProblem d, CgVec<T
       di[j] = v.dinv[row];
     }
   }
-  T alpha;
-  if (d.alpha_ready) {
-    alpha = (T)d.st.alpha[s];
-  } else {
-    const int64_t c0 = d.sub_part0[s];
-    const double pq = warp_sum_parts(d.part0, c0, d.sub_part0[s + 1] - c0);
-    alpha = (pq > 0.0 && isfinite(pq)) ? (T)(d.st.rho[s] / pq) : T(0);
-  }
+  const T alpha = (T)d.st.alpha[s];   // formed by the step's SpMV kernel (cg_alpha_ticket)
   const T sc = sizeof(T) == 4 ? (T)d.st.sc[s] : T(1);
   T a = T(0), b = T(0);
 #pragma unroll
@@ -460,14 +447,7 @@ __global__ void __launch_bounds__(kTileRows) k_cg_update32(DevProblem d, CgVec<f
       di[h] = *reinterpret_cast<const float4*>(v.dinv + r0 + o);
     }
   }
-  float alpha;
-  if (d.alpha_ready) {
-    alpha = (float)d.st.alpha[s];
-  } else {
-    const int64_t c0 = d.sub_part0[s];
-    const double pq = warp_sum_parts(d.part0, c0, d.sub_part0[s + 1] - c0);
-    alpha = (pq > 0.0 && isfinite(pq)) ? (float)(d.st.rho[s] / pq) : 0.f;
-  }
+  const float alpha = (float)d.st.alpha[s];   // formed by the step's SpMV kernel
   const float sc = d.st.sc[s];
   float a = 0.f, b = 0.f;
 #pragma unroll

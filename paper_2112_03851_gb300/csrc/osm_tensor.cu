@@ -411,7 +411,6 @@ DevProblem fp32_view(const DevProblem& d) {
   v.ub_tile0 = d.box_ub_tile0;
   v.sub_ub0 = d.box_sub_ub0;
   v.n_ublocks = d.box_n_ublocks;
-  v.alpha_ready = 1;   // the tensor kernel's last CTA per subdomain forms p.q and alpha
   v.sub_part0 = d.sub_cta0;
   return v;
 }
