@@ -89,6 +89,11 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Fused multiply-add in the kernel's own precision (fmaf for float: no
+// detour through double).
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+
 // Modes of the tensor kernel.
 constexpr int kTxCgStep = 0;   // FP32: one step of the inner CG (t = A z and the direction epilogue)
 constexpr int kTxApply = 1;    // FP32: y = A x
@@ -283,8 +288,8 @@ __global__ void __launch_bounds__(kTileRows, sizeof(T) == 4 ? 3 : 2)
 #pragma unroll
               for (int b = 0; b < 5; ++b) {
                 const T v = S[st][idx + b * nx];
-                sm = fma(cy[b], v, sm);
-                sk = fma(cy[5 + b], v, sk);
+                sm = fma_t(cy[b], v, sm);
+                sk = fma_t(cy[5 + b], v, sk);
               }
               TM[ypad[m]] = sm;
               TK[ypad[m]] = sk;
@@ -299,8 +304,8 @@ __global__ void __launch_bounds__(kTileRows, sizeof(T) == 4 ? 3 : 2)
 #pragma unroll
           for (int a = 0; a < 5; ++a) {
             const T tm = TM[xbase + a], tk = TK[xbase + a];
-            P = fma(kx[a], tm, fma(mx[a], tk, P));
-            Q = fma(mx[a], tm, Q);
+            P = fma_t(kx[a], tm, fma_t(mx[a], tk, P));
+            Q = fma_t(mx[a], tm, Q);
           }
         }
         // ring slot u holds plane kk; slot (u + 1 + c) % 5 holds plane kk - 4 + c
@@ -312,7 +317,7 @@ __global__ void __launch_bounds__(kTileRows, sizeof(T) == 4 ? 3 : 2)
           const T* cz = CZ[k - k0];
           T t = T(0);
 #pragma unroll
-          for (int c = 0; c < 5; ++c) t = fma(cz[c], ph[(u + 1 + c) % 5], fma(cz[5 + c], qh[(u + 1 + c) % 5], t));
+          for (int c = 0; c < 5; ++c) t = fma_t(cz[c], ph[(u + 1 + c) % 5], fma_t(cz[5 + c], qh[(u + 1 + c) % 5], t));
           const bool dir = dcol || ((fm & 16) && k == 0) || ((fm & 32) && k == nz - 1);
           const int64_t row = voff + col + (int64_t)nxy * k;
           if constexpr (MODE == kTxCgStep) {
