@@ -42,7 +42,7 @@ P_ROBIN = 20.0
 # (Sec. 4; osm_sample_p race mode, fewest Schwarz iterations).  regional: 16
 # log-uniform p in [0.8, 3] (SplitMix64 seed 0), mixed form, winner 1.6664
 # at 660 iterations; layered64: 20 from the sweeps of the 64^3 workload.
-P_FOR = {"layered64": 20.0, "regional": 1.6664, "layered160": 40.0, "layered48": 10.0}
+P_FOR = {"layered64": 20.0, "regional": 1.6664, "regional_mid": 1.6664, "layered160": 40.0, "layered48": 10.0}
 RTOL = 1e-8
 INNER_RTOL = 1e-10
 MIXED_INNER_RTOL = 0.4
@@ -122,10 +122,18 @@ def _definitions(text):
 
 
 def _kernel_hash(kernel):
-    """Hash of one kernel's source: its definition and, transitively, the
-    device helpers it calls (osm_kernels.cu, osm_device.cuh)."""
+    """Hash of one kernel's source.  SELL kernels: their definition and,
+    transitively, the device helpers they call (osm_kernels.cu,
+    osm_device.cuh).  The tensor-product kernel (one template for all its
+    modes): osm_tensor.cu with osm_device.cuh."""
     import re
     csrc = os.path.join(ROOT, "paper_2112_03851_gb300", "csrc")
+    if kernel.startswith("k_tensor"):
+        h = hashlib.sha256()
+        for name in ("osm_tensor.cu", "osm_device.cuh"):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+        return h.hexdigest()[:16]
     defs = {}
     for name in ("osm_device.cuh", "osm_kernels.cu"):
         with open(os.path.join(csrc, name)) as f:
@@ -143,17 +151,22 @@ def _kernel_hash(kernel):
     return h.hexdigest()[:16]
 
 
-def _traffic_per_launch(n_local, which, col_bytes):
-    """DRAM bytes per launch of kernel `which` from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "cg_spmv_layered48_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic_regional.json")
+
+
+def _traffic_per_launch(entry, rows):
+    """DRAM bytes (read + write) of one launch of a kernel from the committed
+    ncu capture on the bench workload (profiles/traffic_regional.json), if it
+    was taken on the current kernel source and a launch of the same size
+    (rows: box rows for the tensor kernels, vector rows for SELL); else
+    None."""
     try:
-        with open(path) as f:
+        with open(TRAFFIC_FILE) as f:
             d = json.load(f)
-        e = d[which]
-        if e.get("kernel_hash") != _kernel_hash(e["kernel"]) or e.get("col_bytes") != col_bytes:
+        e = d["entries"][entry]
+        if e.get("kernel_hash") != _kernel_hash(e["kernel"]) or int(e["rows"]) != int(rows):
             return None
-        return round(float(e["dram_bytes_per_row"]) * n_local)
+        return int(e["dram_bytes_read"]) + int(e["dram_bytes_write"])
     except Exception:
         return None
 
@@ -454,19 +467,58 @@ def _roofline_alu(sol, ms):
 
 
 def _roofline(sol, prec, name):
-    """Roofline of the CG-step SpMV kernel (prec 2: k_cg_spmv_dir32, 3:
-    k_cg_spmv<double>), timed alone with every subdomain active."""
+    """Roofline of a CG-step kernel timed alone with every subdomain active
+    (prec 2: the FP32 CG step, tensor-product or SELL; 3: k_cg_spmv<double>):
+    algorithmic bytes per launch over the CUDA-event time, against the
+    measured copy bandwidth."""
     ms = sol.profile_spmv(20, prec=prec)
     nbytes = sol.spmv_bytes(prec)
     peak, kind = _peaks()
     achieved = nbytes / (ms / 1e3) / 1e9
+    tensor = prec == 2 and sol.info.get("fp32_operator") == 2
+    if tensor:
+        traffic = _traffic_per_launch("k_tensor_cg_step", sol.info["box_rows"])
+    elif prec == 3:
+        traffic = _traffic_per_launch("k_cg_spmv_double", sol.info["vec_rows"])
+    else:
+        traffic = None
+    out = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+           "frac": round(achieved / peak, 4), "traffic": traffic,
+           "kernel": name, "peak_kind": f"{kind} hbm_gbs (copy), burst (kernel timed alone)",
+           "ms_per_launch": round(ms, 5), "algorithmic_bytes": nbytes}
+    if not tensor:
+        out["col_bytes"] = sol.info["col_bytes_fp64" if prec in (0, 3) else "col_bytes_fp32"]
+    return out
+
+
+# FP64 multiply-adds per box row of the tensor-product operator's sum
+# factorisation: 5-tap bands, y pass 2 x 5, x pass 3 x 5, z pass 2 x 5.
+TENSOR_FMA_PER_ROW = 35
+
+
+def _roofline_fp64_start(sol):
+    """The mixed refinement step's FP64 start (prec 4) timed alone: on the
+    tensor form it is bound by the FP64 FMA pipe (2 flops per multiply-add,
+    TENSOR_FMA_PER_ROW per box row, against the measured FP64 FMA rate); on
+    SELL it is the FP64 SpMV (HBM)."""
+    ms = sol.profile_spmv(20, prec=4)
+    if sol.info.get("fp64_start") == 2:
+        flops = 2.0 * TENSOR_FMA_PER_ROW * sol.info["box_rows"]
+        achieved = flops / (ms / 1e3) / 1e9
+        return {"bound": "alu", "achieved": round(achieved, 1), "peak": FP64_FMA_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": round(achieved / FP64_FMA_PEAK_GFLOPS, 4),
+                "traffic": _traffic_per_launch("k_tensor_fp64_start", sol.info["box_rows"]),
+                "kernel": "k_tensor<double, 2> (FP64 tensor-product defect d = b - A u and FP32 CG start)",
+                "peak_kind": "measured FP64 FMA probe (152 SMs x 2 DFMA/clk x 2.07 GHz = 1.26 TFLOP/s nominal)",
+                "ms_per_launch": round(ms, 5), "algorithmic_flops": flops}
+    nbytes = sol.spmv_bytes(0)
+    peak, kind = _peaks()
+    achieved = nbytes / (ms / 1e3) / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4),
-            "traffic": _traffic_per_launch(sol.info["n_local"], "k_cg_spmv_dir32" if prec == 2 else "k_cg_spmv_double",
-                                           sol.info["col_bytes_fp64" if prec in (0, 3) else "col_bytes_fp32"]),
-            "kernel": name, "peak_kind": f"{kind} hbm_gbs (copy), burst (kernel timed alone)",
-            "ms_per_launch": round(ms, 5), "algorithmic_bytes": nbytes,
-            "col_bytes": sol.info["col_bytes_fp64" if prec in (0, 3) else "col_bytes_fp32"]}
+            "frac": round(achieved / peak, 4), "traffic": None,
+            "kernel": "k_cg_init_mixed (FP64 SELL defect d = b - A u and FP32 CG start)",
+            "peak_kind": f"{kind} hbm_gbs (copy), burst (kernel timed alone)", "ms_per_launch": round(ms, 5),
+            "algorithmic_bytes": nbytes}
 
 
 def _spmv_roofline_sell32(sol):
@@ -563,6 +615,7 @@ def run_ours(args):
                                       _roofline(sol, 2, "k_cg_spmv_dir32 (batched SELL-32 FP32 SpMV of the CG step "
                                                        "+ direction epilogue, every subdomain active)"))
             r["spmv_roofline"] = _spmv_roofline_sell32(sol)
+            r["roofline_fp64_start"] = _roofline_fp64_start(sol)
         else:
             r["roofline_dominant"] = _roofline(sol, 3, "k_cg_spmv<double> (batched SELL-32 FP64 SpMV of the CG "
                                                        "step, every subdomain active)")
@@ -588,6 +641,7 @@ def run_ours(args):
             "roofline": h["roofline_dominant"]}
     if "spmv_roofline" in h:
         line["spmv_roofline"] = h["spmv_roofline"]
+        line["roofline_fp64_start"] = h["roofline_fp64_start"]
     if tune_rec is not None:
         line["inner_rtol_tuning"] = tune_rec
     keys = ("value", "ms_per_step", "steps", "warmup", "schwarz_iterations", "cg_steps_per_solve", "relres",
@@ -790,23 +844,61 @@ def run_grad(args, pkg, ws, rank, local, barrier):
 
 
 def profile_iteration(args):
-    """One Schwarz iteration of the bench workload (a few hundred kernel
-    launches), in the precision and launch mode given."""
+    """One Schwarz iteration of a workload (a few dozen to a few hundred
+    kernel launches) after args.warm_iterations untimed ones, in the
+    precision and launch mode given, between cudaProfilerStart and
+    cudaProfilerStop (ncu --profile-from-start off captures just that
+    iteration)."""
     import torch
 
     import gen
     import paper_2112_03851_gb300 as pkg
     torch.cuda.set_device(0)
-    prob = gen.workload(args.workload or WORKLOAD)
+    name = args.workload or WORKLOAD
+    prob = gen.workload(name)
     prec = "mixed" if args.prec == "both" else args.prec
-    sol = pkg.Solver.from_problem(prob, p=P_ROBIN, inner_rtol=INNER_RTOL, max_outer=5000, prec=prec,
+    sol = pkg.Solver.from_problem(prob, p=P_FOR.get(name, P_ROBIN), inner_rtol=INNER_RTOL, max_outer=5000, prec=prec,
                                   mixed_inner_rtol=MIXED_INNER_RTOL,
                                   use_graph=0 if args.launch == "host" else 1)
     sol.reset()
+    if args.warm_iterations:
+        sol.iterate(args.warm_iterations)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
     hist = sol.iterate(1)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     st = sol.stats()
-    print(json.dumps({"profile_iteration": args.workload or WORKLOAD, "prec": prec, "relres": float(hist[0]),
-                      **st}), flush=True)
+    print(json.dumps({"profile_iteration": name, "prec": prec, "warm_iterations": args.warm_iterations,
+                      "relres": float(hist[0]), "fp32_operator": sol.info.get("fp32_operator"),
+                      "fp64_start": sol.info.get("fp64_start"), **st}), flush=True)
+    return 0
+
+
+def profile_kernel(args):
+    """The kernel osm_profile_spmv times for `--profile-kernel PREC` (2: the
+    FP32 CG step, 3: the FP64 CG-step SpMV, 4: the FP64 start of a mixed
+    refinement step) on a workload: 20 untimed and 5 timed launches with
+    every subdomain active, between cudaProfilerStart and cudaProfilerStop."""
+    import torch
+
+    import gen
+    import paper_2112_03851_gb300 as pkg
+    torch.cuda.set_device(0)
+    name = args.workload or WORKLOAD
+    prob = gen.workload(name)
+    prec = "fp64" if args.profile_kernel == 3 else "mixed"
+    sol = pkg.Solver.from_problem(prob, p=P_FOR.get(name, P_ROBIN), inner_rtol=INNER_RTOL, max_outer=5000, prec=prec,
+                                  mixed_inner_rtol=MIXED_INNER_RTOL)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
+    ms = sol.profile_spmv(1, prec=args.profile_kernel)
+    torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
+    i = sol.info
+    print(json.dumps({"profile_kernel": args.profile_kernel, "workload": name, "ms": ms, "box_rows": i.get("box_rows"),
+                      "vec_rows": i["vec_rows"], "fp32_operator": i.get("fp32_operator"),
+                      "fp64_start": i.get("fp64_start")}), flush=True)
     return 0
 
 
@@ -847,12 +939,19 @@ def main(argv=None):
                     help="host: launch the same kernels one by one (for ncu, which cannot attribute "
                          "kernels inside graphs with conditional nodes)")
     ap.add_argument("--profile-iteration", action="store_true",
-                    help="set up the workload, run one Schwarz iteration and exit (for ncu captures)")
+                    help="set up the workload, run --warm-iterations untimed Schwarz iterations, then one inside a "
+                         "cudaProfilerStart/Stop range, and exit (for ncu captures)")
+    ap.add_argument("--warm-iterations", type=int, default=0)
+    ap.add_argument("--profile-kernel", type=int, choices=(2, 3, 4), default=None,
+                    help="set up the workload and launch the kernel osm_profile_spmv times for this prec inside a "
+                         "cudaProfilerStart/Stop range (for ncu captures)")
     ap.add_argument("--profile-sample", action="store_true",
                     help="set up the workload, run two Schwarz iterations of a 32-candidate p batch and exit")
     args = ap.parse_args(argv)
     if args.profile_iteration:
         return profile_iteration(args)
+    if args.profile_kernel is not None:
+        return profile_kernel(args)
     if args.profile_sample:
         return profile_sample(args)
     if args.impl == "reference":

@@ -335,6 +335,12 @@ def workload(name: str) -> Problem:
         return layered_problem(32, 4, p=20.0, seed=0)
     if name == "regional":
         return regional_problem()
+    if name == "regional_mid":
+        # the regional workload's subdomain sizes and grading on a quarter of
+        # its area and a third of its depth: 8 x 8 x 1 subdomains (profiling
+        # captures that must stay at a few GB on the device)
+        return regional_problem(nx=128, ny=128, nz=16, sx=8, sy=8, sz=1, p=1.6664, seed=0, lx=100.0, ly=100.0,
+                                lz=10.0)
     if name == "layered160":
         return layered_problem(160, 8, p=10.0, seed=0)
     if name in ("slab32", "slab64", "slab128"):
@@ -342,5 +348,5 @@ def workload(name: str) -> Problem:
     raise KeyError(name)
 
 
-WORKLOADS = ("sphere16", "layered32", "layered64", "layered48", "regional", "layered160",
+WORKLOADS = ("sphere16", "layered32", "layered64", "layered48", "regional", "regional_mid", "layered160",
              "slab32", "slab64", "slab128")

@@ -415,18 +415,23 @@ osm_status osm_host_local_system_tc(const osm_mesh *mesh, const double *drho, co
 osm_status osm_host_face_stiffness(const osm_mesh *mesh, const double *drho, const osm_decomp *dec, int32_t face,
                                    double *val);
 
-/* Time one batched SELL SpMV kernel alone over every subdomain.
- *   prec 0: the plain FP64 operator y = A x (the stop test's SpMV);
- *   prec 1: the plain FP32 operator of the mixed inner solve;
- *   prec 2: the FP32 CG-step kernel k_cg_spmv_dir32 (SpMV of z plus the
- *           p, q direction epilogue and the p.q partials);
- *   prec 3: the FP64 CG-step kernel k_cg_spmv<double> (SpMV of p, p.q).
- * 1 and 2 need an OSM_MIXED handle (else OSM_E_STATE).  After 20 untimed
+/* Time one operator kernel alone over every subdomain.
+ *   prec 0: the plain FP64 SELL operator y = A x (the SpMV of the FP64 paths);
+ *   prec 1: the plain FP32 operator of the mixed inner solve (SELL, or the
+ *           tensor-product kernel when osm_info fp32_operator is 2);
+ *   prec 2: the FP32 CG-step kernel (k_cg_spmv_dir32 or its tensor-product
+ *           counterpart: the operator plus the p, q direction epilogue and
+ *           the p.q partials);
+ *   prec 3: the FP64 CG-step kernel k_cg_spmv<double> (SpMV of p, p.q);
+ *   prec 4: the start of a mixed refinement step (the FP64 defect d = b - A u
+ *           with the FP32 CG start; SELL or tensor-product, osm_info
+ *           fp64_start).
+ * 1, 2 and 4 need an OSM_MIXED handle (else OSM_E_STATE).  After 20 untimed
  * launches, 5 trials of `reps` back-to-back launches are timed with CUDA
  * events on the handle's stream; *ms receives the median time per launch in
- * milliseconds (host).  0 and 1 use the work vectors only; 2 and 3 mark
- * every subdomain active and overwrite the CG vectors and scalars, so call
- * them between solves (the next osm_solve starts afresh). */
+ * milliseconds (host).  0 and 1 use the work vectors only; 2, 3 and 4
+ * overwrite the CG vectors and scalars (2 and 3 mark every subdomain
+ * active), so call them between solves (the next osm_solve starts afresh). */
 osm_status osm_profile_spmv(osm_handle h, int32_t prec, int32_t reps, double *ms);
 
 /*

@@ -1718,15 +1718,16 @@ osm_status osm_host_face_system(const osm_mesh* mesh, const double* drho, const 
 }
 
 osm_status osm_profile_spmv(osm_handle h, int32_t prec, int32_t reps, double* ms) {
-  if (!h || !ms || reps < 1 || prec < 0 || prec > 3) return OSM_E_ARG;
-  if ((prec == 1 || prec == 2) && h->opts.prec != OSM_MIXED)
-    return fail(h, OSM_E_STATE, "prec 1 and 2 need an OSM_MIXED handle");
+  if (!h || !ms || reps < 1 || prec < 0 || prec > 4) return OSM_E_ARG;
+  if ((prec == 1 || prec == 2 || prec == 4) && h->opts.prec != OSM_MIXED)
+    return fail(h, OSM_E_STATE, "prec 1, 2 and 4 need an OSM_MIXED handle");
   if (prec >= 2) OSM_CUDA(h, launch_profile_state(h->d, h->stream));
   auto launch = [&]() {
     switch (prec) {
       case 0: return launch_spmv_plain(h->d, h->d.w, h->d.y, h->stream);
       case 1: return launch_spmv_plain32(h->d, h->d.z32, h->d.q32, h->stream);
       case 2: return launch_cg_spmv_alone(h->d, 1, h->stream);
+      case 4: return launch_cg_start(h->d, h->stream, 1);
       default: return launch_cg_spmv_alone(h->d, 0, h->stream);
     }
   };

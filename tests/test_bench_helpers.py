@@ -7,7 +7,8 @@ import bench
 
 
 class _FakeSolver:
-    info = {"nnz": 129_600_000, "n_local": 2_197_000, "n_slices": 70_000, "col_bytes_fp64": 4, "col_bytes_fp32": 2}
+    info = {"nnz": 129_600_000, "n_local": 2_197_000, "n_slices": 70_000, "col_bytes_fp64": 4, "col_bytes_fp32": 2,
+            "vec_rows": 2_200_000, "box_rows": 0, "fp32_operator": 1}
 
     def spmv_bytes(self, prec=0):
         vb = 8 if prec in (0, 3) else 4
@@ -30,13 +31,15 @@ def test_hbm_roofline_fields():
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["ms_per_launch"] == 0.25
     assert r["algorithmic_bytes"] == _FakeSolver().spmv_bytes(3)
     assert abs(r["achieved"] - r["algorithmic_bytes"] / 0.25e-3 / 1e9) < 0.1
+    assert r["traffic"] is None                      # another launch size than the committed capture
 
 
 def test_traffic_key_matches_the_committed_capture():
-    """The committed ncu traffic of the FP32 CG-step SpMV is keyed to its
-    current source: editing that kernel (or a helper it calls) drops it."""
-    d = json.loads((Path(bench.ROOT) / "profiles" / "cg_spmv_layered48_traffic.json").read_text())
-    e = d["k_cg_spmv_dir32"]
-    assert e["kernel_hash"] == bench._kernel_hash("k_cg_spmv_dir32")
-    assert bench._traffic_per_launch(1000, "k_cg_spmv_dir32", e["col_bytes"]) == round(e["dram_bytes_per_row"] * 1000)
-    assert bench._traffic_per_launch(1000, "k_cg_spmv_dir32", 4 if e["col_bytes"] == 2 else 2) is None
+    """The committed ncu traffic of the bench workload's kernels is keyed to
+    their current source and launch size: editing a kernel (or a helper it
+    calls), or another workload, drops it."""
+    d = json.loads(Path(bench.TRAFFIC_FILE).read_text())
+    for name, e in d["entries"].items():
+        assert e["kernel_hash"] == bench._kernel_hash(e["kernel"]), name
+        assert bench._traffic_per_launch(name, e["rows"]) == e["dram_bytes_read"] + e["dram_bytes_write"]
+        assert bench._traffic_per_launch(name, e["rows"] + 256) is None
