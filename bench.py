@@ -358,6 +358,7 @@ def _measure(sol, prob, warmup, steps, e2e_steps, ws, local, barrier, use_graph_
         "value": value, "ms_per_step": ms_max, "steps": steps, "warmup": max(warmup, 1), "relres": rel,
         "schwarz_iterations": st["n_outer"], "cg_steps_per_solve": st["n_cg_steps"],
         "launches_per_step": int(st["n_launches"]), "gpu_launches": int(launches),
+        "op_row_steps": int(st["op_row_steps"]), "sub_row_steps": int(st["sub_row_steps"]),
         "clocks": clk.summary(), "launch_mode": use_graph_note,
         "_phi": phi.cpu().numpy(),
     }
@@ -521,6 +522,51 @@ def _roofline_fp64_start(sol):
             "algorithmic_bytes": nbytes}
 
 
+# Algorithmic bytes per row of the CG-step kernels, per CG step of a
+# subdomain: the FP32 update (k_cg_update32) reads p, x, q, r and D^-1 and
+# writes x, r and z (4 B each); the FP64 update (k_cg_update_a) the same in
+# 8 B, and the FP64 direction (k_cg_direction) reads z and p and writes p.
+UPD32_BYTES_PER_ROW = 32
+UPD64_BYTES_PER_ROW = 64
+DIR64_BYTES_PER_ROW = 24
+# Per Schwarz iteration of the mixed form on the tensor-product form, per box
+# row: the FP64 start reads u, b, D^-1 (FP32) and the box-to-vector map and
+# writes y, r, z and x (FP32); the correction reads x and u and writes u and
+# its box mirror.
+MIXED_OUTER_BYTES_PER_ROW = 44 + 28
+
+
+def _solve_hbm(sol, prec, m):
+    """Solve-level HBM fraction: algorithmic bytes of one solve over its
+    measured time.  Counted: the CG-step kernels at the rows they actually
+    processed (osm_stats op_row_steps: each subdomain's CG steps times the
+    rows its kernels sweep) and, for the mixed form on the tensor-product
+    operator, the FP64 start and correction once per Schwarz iteration.  Not
+    counted: the exchange, the averaging and the stop test (interface rows
+    and a few vector sweeps per Schwarz iteration), so this is a lower bound."""
+    i = sol.info
+    rows = m["op_row_steps"]
+    if prec == "mixed" and i.get("fp32_operator") == 2:
+        per_row = sol.spmv_bytes(2) / i["box_rows"] + UPD32_BYTES_PER_ROW
+        outer = MIXED_OUTER_BYTES_PER_ROW * i["box_rows"] * m["schwarz_iterations"]
+        counted = "tensor CG step + FP32 update at the rows processed; FP64 start + correction per Schwarz iteration"
+    elif prec == "mixed":
+        per_row = sol.spmv_bytes(2) / i["vec_rows"] + UPD32_BYTES_PER_ROW
+        outer = 0
+        counted = "SELL FP32 CG step + FP32 update at the rows processed"
+    else:
+        per_row = sol.spmv_bytes(3) / i["vec_rows"] + UPD64_BYTES_PER_ROW + DIR64_BYTES_PER_ROW
+        outer = 0
+        counted = "SELL FP64 CG step (SpMV, update, direction) at the rows processed"
+    nbytes = per_row * rows + outer
+    peak, kind = _peaks()
+    achieved = nbytes / (m["ms_per_step"] / 1e3) / 1e9
+    return {"bytes_per_solve": int(nbytes), "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "op_row_steps": rows, "counted": counted,
+            "peak_kind": f"{kind} hbm_gbs (copy)", "note": "lower bound: per-iteration exchange, averaging and "
+            "stop-test kernels not counted"}
+
+
 def _spmv_roofline_sell32(sol):
     """The FP32 SELL CG-step SpMV (k_cg_spmv_dir32) from the autotuner's
     timing of its fastest variant (CUDA events, timed alone, every subdomain
@@ -620,6 +666,7 @@ def run_ours(args):
             r["roofline_dominant"] = _roofline(sol, 3, "k_cg_spmv<double> (batched SELL-32 FP64 SpMV of the CG "
                                                        "step, every subdomain active)")
             r["roofline_alu"] = _roofline_alu(sol, r["roofline_dominant"]["ms_per_launch"])
+        r["solve_hbm"] = _solve_hbm(sol, prec, r)
         del sol
         torch.cuda.empty_cache()
     h = res[head]
@@ -638,7 +685,7 @@ def run_ours(args):
             "gpu_launches": h["gpu_launches"], "schwarz_iterations": h["schwarz_iterations"],
             "cg_steps_per_solve": h["cg_steps_per_solve"], "relres": h["relres"],
             "setup_s": h["setup_s"], "e2e": h["e2e"], "clocks": h["clocks"],
-            "roofline": h["roofline_dominant"]}
+            "roofline": h["roofline_dominant"], "solve_hbm": h["solve_hbm"]}
     if "spmv_roofline" in h:
         line["spmv_roofline"] = h["spmv_roofline"]
         line["roofline_fp64_start"] = h["roofline_fp64_start"]
@@ -652,6 +699,7 @@ def run_ours(args):
         line["fp64"]["precision"] = f"FP64, subdomain PCG to {INNER_RTOL:g} of ||b_i|| every iteration (Sec. 6)"
         line["fp64"]["roofline"] = f["roofline_dominant"]
         line["fp64"]["roofline_alu"] = f["roofline_alu"]
+        line["fp64"]["solve_hbm"] = f["solve_hbm"]
         line["mixed_speedup_vs_fp64"] = round(h["value"] / f["value"], 3)
         line["mixed_vs_fp64_rel_l2"] = float(
             __import__("numpy").linalg.norm(h["_phi"] - f["_phi"]) / __import__("numpy").linalg.norm(f["_phi"]))
@@ -661,6 +709,7 @@ def run_ours(args):
         line["fp64_refine"]["precision"] = (f"FP64, the mixed form's algorithm: subdomain CG to "
                                             f"{tin:g} of each iteration's defect")
         line["fp64_refine"]["roofline"] = f["roofline_dominant"]
+        line["fp64_refine"]["solve_hbm"] = f["solve_hbm"]
         if head == "mixed":
             line["mixed_speedup_vs_fp64_refine"] = round(h["value"] / f["value"], 3)
     # error of every result against the FP64 oracle's monolithic solve

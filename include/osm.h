@@ -175,6 +175,11 @@ typedef struct {
     double relres;          /* last stop-test value */
     int32_t status;         /* bit 0: a subdomain CG hit max_inner; bit 1: CG breakdown */
     int32_t reserved;
+    int64_t sub_row_steps;  /* osm_solve / osm_iterate: sum over subdomains of (CG steps of the
+                               call) x (its local unknowns); 0 after osm_sample_p */
+    int64_t op_row_steps;   /* the same with the rows the CG-step kernels sweep per step: the
+                               box layout's rows (tiles of 256) on the FP32 tensor-product form,
+                               the padded SELL rows otherwise */
 } osm_stats_t;
 
 /* Fill *o with the defaults listed in osm_opts. */

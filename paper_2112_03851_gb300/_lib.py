@@ -70,7 +70,8 @@ def _info_dict(info):
 
 class OsmStats(C.Structure):
     _fields_ = [("n_outer", C.c_int32), ("n_cg_steps", C.c_int32), ("n_launches", C.c_int64),
-                ("relres", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32)]
+                ("relres", C.c_double), ("status", C.c_int32), ("reserved", C.c_int32),
+                ("sub_row_steps", C.c_int64), ("op_row_steps", C.c_int64)]
 
 
 class OsmError(RuntimeError):

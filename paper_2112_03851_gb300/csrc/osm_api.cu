@@ -166,7 +166,7 @@ osm_status upload_problem(osm_ctx* h) {
   OSM_CUDA(h, dalloc(h, &d.psub, ns));
   DevSubState& st = d.st;
   for (double** v : {&st.rho, &st.alpha, &st.beta, &st.bb, &st.rr}) OSM_CUDA(h, dalloc(h, v, ns));
-  for (int32_t** v : {&st.active, &st.iters, &st.status}) OSM_CUDA(h, dalloc(h, v, ns));
+  for (int32_t** v : {&st.active, &st.iters, &st.status, &st.tsteps}) OSM_CUDA(h, dalloc(h, v, ns));
   OSM_CUDA(h, dalloc(h, &st.ucnt, ns));
   OSM_CUDA(h, dalloc(h, &st.tcnt, ns));
   OSM_CUDA(h, dalloc(h, &st.pq, ns));
@@ -807,6 +807,7 @@ osm_status run_iterations(osm_ctx* h, double rtol, int max_outer) {
   h->ctl_host->running = h->hp.n_inst;
   OSM_CUDA(h, cudaMemsetAsync(h->d.inst_done, 0, sizeof(int32_t) * h->hp.n_inst, h->stream));
   OSM_CUDA(h, cudaMemsetAsync(h->d.inst_iters, 0, sizeof(int32_t) * h->hp.n_inst, h->stream));
+  OSM_CUDA(h, cudaMemsetAsync(h->d.st.tsteps, 0, sizeof(int32_t) * h->hp.nsub, h->stream));
   OSM_CUDA(h, cudaMemsetAsync(h->d.inst_relres, 0, sizeof(double) * h->hp.n_inst, h->stream));
   OSM_CUDA(h, cudaMemcpyAsync(h->d.ctl, h->ctl_host, sizeof(DevCtl), cudaMemcpyHostToDevice, h->stream));
   OSM_CUDA(h, launch_load_nodes(h->d, h->stream));
@@ -1291,6 +1292,24 @@ osm_status osm_stats(osm_handle h, osm_stats_t* o) {
   o->relres = c.relres;
   o->status = c.status;
   o->reserved = 0;
+  // rows the CG-step kernels processed: each subdomain's CG steps times its
+  // local unknowns, and times the rows its CG-step kernels sweep (the box
+  // layout's tiles on the FP32 tensor-product form, the padded SELL rows
+  // otherwise)
+  o->sub_row_steps = 0;
+  o->op_row_steps = 0;
+  if (h->last_kind == 0) {
+    const int ns = h->hp.nsub;
+    std::vector<int32_t> steps(ns);
+    OSM_CUDA(h, cudaMemcpy(steps.data(), h->d.st.tsteps, sizeof(int32_t) * ns, cudaMemcpyDeviceToHost));
+    const bool box = h->opts.prec == OSM_MIXED && h->d.t32;
+    for (int s = 0; s < ns; ++s) {
+      const SubInfo& S = h->hp.sub[s];
+      const int64_t op = box ? (h->hp.box_sub_tile0[s + 1] - h->hp.box_sub_tile0[s]) * kTileRows : S.npad;
+      o->sub_row_steps += (int64_t)steps[s] * S.n;
+      o->op_row_steps += (int64_t)steps[s] * op;
+    }
+  }
   return OSM_OK;
 }
 

@@ -190,6 +190,7 @@ struct DevSubState {
   double* rr;       // ||r||^2
   int32_t* active;  // 1 while the subdomain's CG runs
   int32_t* iters;   // CG iterations of the current solve
+  int32_t* tsteps;  // CG steps of the subdomain summed over the current call's Schwarz iterations
   int32_t* status;  // 0 ok, 1 cap reached, 2 breakdown
   unsigned* ucnt;   // per-subdomain ticket of the CG update's blocks (reset by the last)
   unsigned* tcnt;   // per-subdomain ticket of the tensor kernel's CTAs (reset by the last)

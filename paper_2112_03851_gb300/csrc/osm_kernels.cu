@@ -218,6 +218,7 @@ __device__ __forceinline__ void cg_step_finish(DevProblem& d, const int64_t* __r
   if (lane == 0) {
     const int it = d.st.iters[s] + 1;
     d.st.iters[s] = it;
+    d.st.tsteps[s] += 1;
     d.st.rr[s] = rr;
     if (!(pq > 0.0) || !isfinite(pq)) {
       d.st.status[s] |= 2;

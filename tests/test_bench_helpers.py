@@ -43,3 +43,21 @@ def test_traffic_key_matches_the_committed_capture():
         assert e["kernel_hash"] == bench._kernel_hash(e["kernel"]), name
         assert bench._traffic_per_launch(name, e["rows"]) == e["dram_bytes_read"] + e["dram_bytes_write"]
         assert bench._traffic_per_launch(name, e["rows"] + 256) is None
+
+
+def test_solve_level_fraction_counts_the_rows_processed():
+    """bytes per solve = (CG-step bytes per row) x (rows the CG-step kernels
+    processed) [+ the mixed tensor form's per-iteration start]; the fraction
+    is those bytes over the solve time against the copy bandwidth."""
+    sol = _FakeSolver()
+    m = {"op_row_steps": 1_000_000_000, "schwarz_iterations": 100, "ms_per_step": 1000.0}
+    r = bench._solve_hbm(sol, "fp64", m)
+    per_row = sol.spmv_bytes(3) / sol.info["vec_rows"] + bench.UPD64_BYTES_PER_ROW + bench.DIR64_BYTES_PER_ROW
+    assert r["bytes_per_solve"] == int(per_row * 1e9)
+    peak, _ = bench._peaks()
+    assert abs(r["frac"] - r["bytes_per_solve"] / 1.0 / 1e9 / peak) < 1e-4
+    sol.info = dict(sol.info, fp32_operator=2, box_rows=2_300_000)
+    sol.spmv_bytes = lambda prec=0: sol.info["box_rows"] * (8 + (12 if prec == 2 else 0))
+    r = bench._solve_hbm(sol, "mixed", m)
+    want = (20 + bench.UPD32_BYTES_PER_ROW) * 1e9 + bench.MIXED_OUTER_BYTES_PER_ROW * 2_300_000 * 100
+    assert abs(r["bytes_per_solve"] - want) <= 1 and "tensor" in r["counted"]

@@ -231,3 +231,19 @@ def test_spmv_variants_agree(osm):
     phis = [sol.solve(rtol=1e-11)[0] for sol in sols]
     for ph in phis[1:]:
         assert float((ph - phis[0]).norm() / phis[0].norm()) <= 1e-9
+
+
+def test_regional_fp64_iterations_match_oracle(osm):
+    """The regional workload (6.18M unknowns, 192 uneven subdomains) in FP64
+    at the bench's Robin p: the Schwarz iteration count is that of the
+    oracle's sequential Jacobi-type Schwarz iteration (tests/golden, written
+    by make_iterations.py from oracle/ only) within one, as the batched CG's
+    reduction order may move the last iteration across the stopping line."""
+    import json
+    from pathlib import Path
+    g = json.loads((Path(__file__).parent / "golden" / "regional_iterations.json").read_text())
+    prob = gen.workload("regional")
+    sol = osm.Solver.from_problem(prob, p=g["p"], inner_rtol=g["inner_rtol"], max_outer=2000)
+    phi, n, rel = sol.solve(rtol=g["rtol"])
+    assert abs(n - g["schwarz_iterations"]) <= 1, (n, g["schwarz_iterations"])
+    assert rel <= g["rtol"]
