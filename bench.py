@@ -497,12 +497,31 @@ def _roofline(sol, prec, name):
 TENSOR_FMA_PER_ROW = 35
 
 
+# FP32 operations per box row of the double-float sum factorisation: 12 per
+# compensated multiply-add (product split by one FMA, two cross-term FMAs, a
+# two-sum and the error gathering) and 3 per renormalisation of the four
+# intermediate sums (My z, K~y z, P, Q).
+DF_OPS_PER_ROW = TENSOR_FMA_PER_ROW * 12 + 4 * 3
+FP32_OPS_PEAK_G = 73300.0 / 2   # measured FP32 FMA rate (profiles/peaks.md) in G lane operations per second
+
+
 def _roofline_fp64_start(sol):
-    """The mixed refinement step's FP64 start (prec 4) timed alone: on the
-    tensor form it is bound by the FP64 FMA pipe (2 flops per multiply-add,
-    TENSOR_FMA_PER_ROW per box row, against the measured FP64 FMA rate); on
-    SELL it is the FP64 SpMV (HBM)."""
+    """The mixed refinement step's start (prec 4) timed alone: on the tensor
+    form in FP64 it is bound by the FP64 FMA pipe (2 flops per multiply-add,
+    TENSOR_FMA_PER_ROW per box row, against the measured FP64 FMA rate); in
+    double-float arithmetic by FP32 issue (DF_OPS_PER_ROW FP32 operations per
+    box row against the measured FP32 FMA rate); on SELL it is the FP64 SpMV
+    (HBM)."""
     ms = sol.profile_spmv(20, prec=4)
+    if sol.info.get("fp64_start") == 3:
+        ops = float(DF_OPS_PER_ROW) * sol.info["box_rows"]
+        achieved = ops / (ms / 1e3) / 1e9
+        return {"bound": "alu", "achieved": round(achieved, 1), "peak": FP32_OPS_PEAK_G, "unit": "G FP32 ops/s",
+                "frac": round(achieved / FP32_OPS_PEAK_G, 4),
+                "traffic": _traffic_per_launch("k_tensor_df_start", sol.info["box_rows"]),
+                "kernel": "k_tensor<Df, 2> (double-float tensor-product defect d = b - A u and FP32 CG start)",
+                "peak_kind": "measured FP32 FMA probe (152 SMs x 128 FFMA/clk x 2.07 GHz = 40.3 T lane ops/s "
+                             "nominal)", "ms_per_launch": round(ms, 5), "algorithmic_fp32_ops": ops}
     if sol.info.get("fp64_start") == 2:
         flops = 2.0 * TENSOR_FMA_PER_ROW * sol.info["box_rows"]
         achieved = flops / (ms / 1e3) / 1e9
@@ -530,10 +549,10 @@ UPD32_BYTES_PER_ROW = 32
 UPD64_BYTES_PER_ROW = 64
 DIR64_BYTES_PER_ROW = 24
 # Per Schwarz iteration of the mixed form on the tensor-product form, per box
-# row: the FP64 start reads u, b, D^-1 (FP32) and the box-to-vector map and
-# writes y, r, z and x (FP32); the correction reads x and u and writes u and
-# its box mirror.
-MIXED_OUTER_BYTES_PER_ROW = 44 + 28
+# row: the start reads u (8 B, FP64 or a float pair), b, D^-1 (FP32) and the
+# box-to-vector map and writes y, r, z and x (FP32); the correction reads x
+# and u and writes u and its two box mirrors (FP64 and float pairs).
+MIXED_OUTER_BYTES_PER_ROW = 44 + 36
 
 
 def _solve_hbm(sol, prec, m):
@@ -655,6 +674,8 @@ def run_ours(args):
         res[prec] = r
         if prec == "mixed":
             r["fp32_operator"] = {1: "SELL-32 matrix", 2: "tensor-product (matrix-free)"}.get(sol.info["fp32_operator"])
+            r["fp64_start"] = {1: "FP64 SELL SpMV", 2: "FP64 tensor-product kernel",
+                               3: "double-float tensor-product kernel (~48-bit)"}.get(sol.info["fp64_start"])
             r["roofline_dominant"] = (_roofline(sol, 2, "k_tensor32 (tensor-product FP32 operator of the CG step + "
                                                        "direction epilogue, every subdomain active)")
                                       if sol.info["fp32_operator"] == 2 else
@@ -676,9 +697,9 @@ def run_ours(args):
             "dtype": "f32 inner CG + f64 refinement" if head == "mixed" else "f64",
             "data": "synthetic",
             "config": {"workload": _workload_desc(prob, p_robin, name, tc),
-                       "precision": (f"mixed: FP32 subdomain CG to {tin:g} of the FP64 defect "
-                                     f"({h.get('fp32_operator')} operator), FP64 defect, exchange and stop test"
-                                     if head == "mixed" else "FP64"),
+                       "precision": (f"mixed: FP32 subdomain CG to {tin:g} of the defect "
+                                     f"({h.get('fp32_operator')} operator), defect by the {h.get('fp64_start')}, "
+                                     f"exchange and stop test in FP64" if head == "mixed" else "FP64"),
                        "l2": "inputs larger than L2 (several GB of subdomain matrices and vectors), no flush",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU",
                        "launch": h["launch_mode"]},

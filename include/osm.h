@@ -121,9 +121,15 @@ typedef struct {
                                handle uses the SELL matrix.  Boxes wider than 128 nodes
                                along x also keep the SELL matrix. */
     int32_t fp64_start;     /* OSM_MIXED with the tensor form: the kernel of each
-                               refinement step's FP64 defect d = b - A u.  0 (default):
-                               chosen by the autotuner; 1: the SELL SpMV; 2: the FP64
-                               tensor-product kernel on a box-layout copy of u */
+                               refinement step's defect d = b - A u.  0 (default):
+                               chosen by the autotuner; 1: the FP64 SELL SpMV; 2: the
+                               tensor-product kernel in FP64 on a box-layout copy of u;
+                               3: the same in double-float arithmetic (pairs of floats,
+                               about 48 significant bits, compensated sums: the FP32
+                               pipe instead of the FP64 one).  The double-float defect's
+                               rounding, about 2^-48 |A| |u| per row, stays some 100x
+                               below a stop tolerance of 1e-8 on these meshes; use 1 or
+                               2 for tolerances below about 1e-10. */
 } osm_opts;
 
 typedef struct {
@@ -158,13 +164,14 @@ typedef struct {
     int32_t reserved_i;
     double tensor_ms_zchunk[4];  /* autotuner timings with z chunks of 8, 16, 32 and 128 planes
                                     (ms, 0 if not run) */
-    int32_t fp64_start;          /* OSM_MIXED: kernel of each refinement step's FP64 defect
-                                    d = b - A u: 1 the SELL SpMV, 2 the FP64 tensor-product
-                                    kernel (chosen by the autotuner with the tensor form); 0
-                                    otherwise */
+    int32_t fp64_start;          /* OSM_MIXED: kernel of each refinement step's defect
+                                    d = b - A u: 1 the FP64 SELL SpMV, 2 the FP64 tensor-
+                                    product kernel, 3 its double-float form (osm_opts
+                                    fp64_start; chosen by the autotuner with the tensor
+                                    form); 0 otherwise */
     int32_t reserved_j;
-    double start_ms[2];          /* autotuner timings of that step: SELL, tensor (ms, 0 if not
-                                    run) */
+    double start_ms[3];          /* autotuner timings of that step: SELL, FP64 tensor,
+                                    double-float tensor (ms, 0 if not run) */
     int64_t box_rows;            /* rows of the box layout of the tensor form (0 if none) */
 } osm_info_t;
 

@@ -57,7 +57,7 @@ class OsmInfo(C.Structure):
                 ("fp32_operator", C.c_int32), ("fp32_operator_tuned", C.c_int32),
                 ("tensor_ms_fp32", C.c_double), ("tensor_zchunk", C.c_int32), ("reserved_i", C.c_int32),
                 ("tensor_ms_zchunk", C.c_double * 4), ("fp64_start", C.c_int32), ("reserved_j", C.c_int32),
-                ("start_ms", C.c_double * 2), ("box_rows", C.c_int64)]
+                ("start_ms", C.c_double * 3), ("box_rows", C.c_int64)]
 
 
 def _info_dict(info):

@@ -59,8 +59,8 @@ struct osm_ctx {
   // tensor-product FP32 operator (mixed handles whose boxes fit the kernel)
   bool have_box = false;
   int fp32_tuned = 1;           // 1: SELL, 2: tensor product (autotuner or opts.fp32_operator)
-  int init_tuned = 0;           // 1: the mixed refinement step starts with the FP64 tensor kernel
-  double tune_init_ms[2] = {};  // autotuner timings of the FP64 refinement start: SELL, tensor
+  int init_tuned = 0;           // the mixed refinement step's start: 0 SELL, 1 FP64 tensor, 2 double-float tensor
+  double tune_init_ms[3] = {};  // autotuner timings of those three
   int zchunk = kZChunks[1];     // z planes per CTA of the tensor kernel (autotuned)
   double tune_tensor_ms = 0.0;
   double tune_zchunk_ms[4] = {};
@@ -308,6 +308,9 @@ osm_status upload_problem(osm_ctx* h) {
       OSM_CUDA(h, upload(h, &box_vec, hp.box_vec));
       d.box_vec = box_vec;
       OSM_CUDA(h, dalloc(h, &d.ub, hp.box_rows));
+      OSM_CUDA(h, dalloc(h, &d.ub2, hp.box_rows));
+      OSM_CUDA(h, dalloc(h, &d.cKdf, hp.band_k.size()));
+      OSM_CUDA(h, dalloc(h, &d.cMdf, hp.band_m.size()));
       OSM_CUDA(h, dalloc(h, &d.cK64, hp.band_k.size()));
       OSM_CUDA(h, dalloc(h, &d.cKp32, hp.band_k.size()));
       OSM_CUDA(h, dalloc(h, &d.dl32, hp.box_rows));
@@ -379,7 +382,7 @@ osm_status select_fp32_operator(osm_ctx* h) {
   for (size_t s = 0; s < h->tc_host.size() / 4; ++s)
     if (h->tc_host[4 * s + 1] != 0.0 || h->tc_host[4 * s + 3] != 0.0) q_zero = false;
   const int want = (h->have_box && h->fp32_tuned == 2 && q_zero) ? 1 : 0;
-  const int want_init = want && h->init_tuned;
+  const int want_init = want ? h->init_tuned : 0;
   if (want == h->d.t32 && want_init == h->d.t64i) return OSM_OK;
   const bool layout_change = want != h->d.t32;
   const bool mirror = want_init && !h->d.t64i;
@@ -583,7 +586,7 @@ osm_status autotune_spmv(osm_ctx* h) {
   h->d.c16_64 = have16;
   h->d.c16_32 = have16 && mixed;
   h->fp32_tuned = (mixed && h->have_box && h->opts.fp32_operator == 2) ? 2 : 1;
-  h->init_tuned = (mixed && h->have_box && h->opts.fp64_start == 2) ? 1 : 0;
+  h->init_tuned = (mixed && h->have_box && h->opts.fp64_start >= 2) ? h->opts.fp64_start - 1 : 0;
   if (h->opts.autotune != 1) return select_fp32_operator(h);
   h->d.t32 = 0;   // the SELL variants first (vectors are zero: no layout to clear)
   OSM_CUDA(h, launch_profile_state(h->d, h->stream));
@@ -639,10 +642,10 @@ osm_status autotune_spmv(osm_ctx* h) {
     }
     if (e == cudaSuccess) e = set_zchunk(h, best_zc);
     h->tune_tensor_ms = best_t;
-    // the mixed refinement step's FP64 start: SELL SpMV or FP64 tensor kernel
-    // (the partial tables follow the kernel); the faster one serves whenever
-    // the tensor layout is in use
-    for (int t = 0; t < 2 && e == cudaSuccess; ++t) {
+    // the mixed refinement step's start: SELL SpMV, FP64 or double-float
+    // tensor kernel (the partial tables follow the kernel); the fastest serves
+    // whenever the tensor layout is in use
+    for (int t = 0; t < 3 && e == cudaSuccess; ++t) {
       h->d.t64i = t;
       h->d.sub_init0 = t ? h->d.sub_cta0 : h->d.sub_tile0;
       for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = launch_cg_start(h->d, h->stream, 1);
@@ -654,8 +657,13 @@ osm_status autotune_spmv(osm_ctx* h) {
       if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
       h->tune_init_ms[t] = ms / 5.0;
     }
-    h->init_tuned = h->opts.fp64_start == 2 ? 1 : h->opts.fp64_start == 1 ? 0
-                                                : (h->tune_init_ms[1] < h->tune_init_ms[0] ? 1 : 0);
+    if (h->opts.fp64_start > 0) {
+      h->init_tuned = h->opts.fp64_start - 1;
+    } else {
+      h->init_tuned = 0;
+      for (int t = 1; t < 3; ++t)
+        if (h->tune_init_ms[t] < h->tune_init_ms[h->init_tuned]) h->init_tuned = t;
+    }
     h->d.t64i = 0;
     h->d.sub_init0 = h->d.sub_tile0;
     h->d.t32 = 0;
@@ -801,8 +809,21 @@ void ctl_reset(osm_ctx* h, double rtol, int max_outer) {
   c.t_limit_ns = (unsigned long long)h->opts.max_seconds * 1000000000ull;
 }
 
+// Stop tolerances below which a solve that would start its refinement steps
+// with the double-float tensor kernel uses the FP64 one instead: the
+// double-float defect's rounding (about 2^-48 |A| |u| per row, 1e-11 to 1e-10
+// of ||f|| on these meshes) would blur a tighter stop test.
+constexpr double kDfStartMinRtol = 1e-9;
+
 // Run Schwarz iterations until relres <= rtol or max_outer iterations.
 osm_status run_iterations(osm_ctx* h, double rtol, int max_outer) {
+  if (h->opts.prec == OSM_MIXED && h->d.t32) {
+    const int start = (h->init_tuned == 2 && rtol > 0.0 && rtol < kDfStartMinRtol) ? 1 : h->init_tuned;
+    if (start != h->d.t64i) {   // both box mirrors are kept current: only the graphs change
+      h->d.t64i = start;
+      drop_graphs(h);
+    }
+  }
   ctl_reset(h, rtol, max_outer);
   h->ctl_host->running = h->hp.n_inst;
   OSM_CUDA(h, cudaMemsetAsync(h->d.inst_done, 0, sizeof(int32_t) * h->hp.n_inst, h->stream));
@@ -895,6 +916,7 @@ osm_status run_sample_batch(osm_ctx* h, int nb, const double* p, double rtol, in
 osm_status reset_state(osm_ctx* h) {
   OSM_CUDA(h, cudaMemsetAsync(h->d.x, 0, sizeof(double) * h->hp.vec_rows, h->stream));
   if (h->d.ub) OSM_CUDA(h, cudaMemsetAsync(h->d.ub, 0, sizeof(double) * h->hp.box_rows, h->stream));
+  if (h->d.ub2) OSM_CUDA(h, cudaMemsetAsync(h->d.ub2, 0, sizeof(float2) * h->hp.box_rows, h->stream));
   if (h->hp.n_fent) OSM_CUDA(h, cudaMemsetAsync(h->d.lam, 0, sizeof(double) * 2 * h->hp.n_fent, h->stream));
   return OSM_OK;
 }
@@ -958,7 +980,7 @@ osm_status osm_setup(const osm_mesh* mesh, const double* drho, const osm_decomp*
   if (!h) return OSM_E_NOMEM;
   if (opts) h->opts = *opts; else osm_default_opts(&h->opts);
   if (!(h->opts.inner_rtol > 0.0) || h->opts.max_outer < 1 || h->opts.max_inner < 1 || h->opts.max_seconds < 1 ||
-      h->opts.fp32_operator < 0 || h->opts.fp32_operator > 2 || h->opts.fp64_start < 0 || h->opts.fp64_start > 2) {
+      h->opts.fp32_operator < 0 || h->opts.fp32_operator > 2 || h->opts.fp64_start < 0 || h->opts.fp64_start > 3) {
     delete h;
     return OSM_E_ARG;
   }
@@ -1028,9 +1050,8 @@ osm_status osm_info(osm_handle h, osm_info_t* o) {
   o->fp32_operator_tuned = h->opts.prec == OSM_MIXED ? h->fp32_tuned : 0;
   o->tensor_ms_fp32 = h->tune_tensor_ms;
   o->tensor_zchunk = h->have_box ? h->zchunk : 0;
-  o->fp64_start = h->opts.prec == OSM_MIXED ? (h->d.t64i ? 2 : 1) : 0;
-  o->start_ms[0] = h->tune_init_ms[0];
-  o->start_ms[1] = h->tune_init_ms[1];
+  o->fp64_start = h->opts.prec == OSM_MIXED ? (h->d.t32 ? h->init_tuned : 0) + 1 : 0;
+  for (int t = 0; t < 3; ++t) o->start_ms[t] = h->tune_init_ms[t];
   for (int c = 0; c < 4; ++c) o->tensor_ms_zchunk[c] = h->tune_zchunk_ms[c];
   o->box_rows = h->have_box ? h->hp.box_rows : 0;
   return OSM_OK;
@@ -1125,7 +1146,7 @@ osm_status osm_setup_batch(int32_t n_inst, const osm_mesh* meshes, const double*
   if (!(h->opts.inner_rtol > 0.0) || h->opts.max_outer < 1 || h->opts.max_inner < 1 || h->opts.max_seconds < 1 ||
       (h->opts.prec != OSM_FP64 && h->opts.prec != OSM_MIXED && h->opts.prec != OSM_FP64_REFINE) ||
       (h->opts.prec != OSM_FP64 && !(h->opts.mixed_inner_rtol > 0.0 && h->opts.mixed_inner_rtol < 1.0)) ||
-      h->opts.fp32_operator < 0 || h->opts.fp32_operator > 2 || h->opts.fp64_start < 0 || h->opts.fp64_start > 2)
+      h->opts.fp32_operator < 0 || h->opts.fp32_operator > 2 || h->opts.fp64_start < 0 || h->opts.fp64_start > 3)
     return fail(h, OSM_E_ARG, "osm_setup_batch: bad options");
   h->stream = (cudaStream_t)cuda_stream;
   auto t0 = std::chrono::steady_clock::now();
@@ -1582,6 +1603,9 @@ osm_status osm_grad_p(osm_handle h, int32_t n_iter, const double* g_obs, double*
     // bbar^n = A^-1 ubar^n
     if (e == cudaSuccess) e = cudaMemcpyAsync(h->d.b, ub, sizeof(double) * nv, cudaMemcpyDeviceToDevice, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->d.x, 0, sizeof(double) * nv, h->stream);
+    // the tensor starts read u from its box-layout mirrors: zero them too
+    if (e == cudaSuccess && h->d.ub) e = cudaMemsetAsync(h->d.ub, 0, sizeof(double) * h->hp.box_rows, h->stream);
+    if (e == cudaSuccess && h->d.ub2) e = cudaMemsetAsync(h->d.ub2, 0, sizeof(float2) * h->hp.box_rows, h->stream);
     if (e != cudaSuccess) { st = fail(h, OSM_E_CUDA, cudaGetErrorString(e)); break; }
     ctl_reset(h, -1.0, 1);
     OSM_CUDA(h, cudaMemcpyAsync(h->d.ctl, h->ctl_host, sizeof(DevCtl), cudaMemcpyHostToDevice, h->stream));

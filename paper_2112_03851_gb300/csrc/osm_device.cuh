@@ -11,6 +11,14 @@
 namespace osm {
 namespace {
 
+// A double as an unevaluated pair of floats, hi + lo (hi the nearest float,
+// lo the nearest float to the remainder): 48 significant bits, exact for the
+// FP32 inputs of the double-float kernels.
+__device__ __forceinline__ float2 df_split(double v) {
+  const float hi = (float)v;
+  return make_float2(hi, (float)(v - (double)hi));
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -311,13 +311,17 @@ struct DevProblem {
   const double *band_k, *band_m;        // plain 1-D bands (5 per band node)
   float *cK32, *cM32;                   // FP32 bands, stiffness with the Robin terms folded in
   float* dinv32b;
-  // FP64 tensor-product start of the mixed form's refinement step (t64i = 1,
-  // only with t32): the iterate u mirrored in the box layout (ub), the vector
-  // row of every box row (box_vec, -1: Dirichlet or padding), FP64 bands
+  // tensor-product start of the mixed form's refinement step (only with t32;
+  // t64i = 1: FP64 arithmetic, 2: double-float arithmetic): the iterate u
+  // mirrored in the box layout (ub; ub2 the same as (hi, lo) float pairs),
+  // the vector row of every box row (box_vec, -1: Dirichlet or padding), the
+  // bands in FP64 and as float pairs
   int32_t t64i;
   double* ub;
+  float2* ub2;
   const int32_t* box_vec;
   double *cK64, *cM64;
+  float2 *cKdf, *cMdf;
   // stop test on the tensor form (handles with a box layout): ubar - u in the
   // box layout (FP32, written by k_average) and the plain FP32 stiffness bands
   float *dl32, *cKp32;
@@ -409,6 +413,7 @@ cudaError_t launch_tensor_coef(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_tensor_dir32(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_tensor_apply32(const DevProblem& d, const float* x, float* y, cudaStream_t s);
 cudaError_t launch_tensor_init64(const DevProblem& d, cudaStream_t s);
+cudaError_t launch_tensor_init_df(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_box_mirror(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_tensor_layer(const DevProblem& d, cudaStream_t s);
 // Shared-memory limits of the tensor kernels (once per process and device).

@@ -577,19 +577,23 @@ __global__ void __launch_bounds__(kTileRows) k_mixed_correct(DevProblem d) {
     if (rb >= 0) {
       const double u = d.x[row] + (double)d.x32[rb];
       d.x[row] = u;
-      if (d.ub) d.ub[rb] = u;   // the box-layout mirror read by the tensor start
+      if (d.ub) d.ub[rb] = u;   // the box-layout mirrors read by the tensor starts
+      if (d.ub2) d.ub2[rb] = df_split(u);
     }
   } else {
     d.x[row] += (double)d.x32[row];
   }
 }
 
-// The iterate u copied into its box-layout mirror (when the FP64 tensor start
-// is switched on for a handle whose iterate is not zero).
+// The iterate u copied into its box-layout mirrors (when a tensor start is
+// switched on for a handle whose iterate is not zero).
 __global__ void __launch_bounds__(kTileRows) k_box_mirror(DevProblem d) {
   const int64_t row = blockIdx.x * (int64_t)kTileRows + threadIdx.x;
   const int32_t rb = d.row_box[row];
-  if (rb >= 0) d.ub[rb] = d.x[row];
+  if (rb >= 0) {
+    if (d.ub) d.ub[rb] = d.x[row];
+    if (d.ub2) d.ub2[rb] = df_split(d.x[row]);
+  }
 }
 
 // y32 = A32 x32 (FP32 values) on every tile: the mixed inner operator.
@@ -965,6 +969,7 @@ cudaError_t launch_box_mirror(const DevProblem& d, cudaStream_t s) {
 }
 
 cudaError_t launch_cg_start(const DevProblem& d, cudaStream_t s, int mixed) {
+  if (mixed && d.t64i == 2) return launch_tensor_init_df(d, s);
   if (mixed && d.t64i) return launch_tensor_init64(d, s);
   if (mixed) OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_cg_init_mixed, s, d);
   else OSM_LAUNCH_RPL(d.rpl64, d.c16_64, k_cg_init, s, d);

@@ -26,6 +26,8 @@
 // bnx (j + bny k).  Rows on the outer boundary are written as zero.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "osm_device.cuh"
 #include "osm_internal.h"
 
@@ -71,6 +73,10 @@ __global__ void k_tensor_coef(DevProblem d) {
       d.cK64[b0 + t] = kv;
       d.cM64[b0 + t] = mv;
     }
+    if (d.cKdf) {
+      d.cKdf[b0 + t] = df_split(kv);
+      d.cMdf[b0 + t] = df_split(mv);
+    }
   }
 }
 
@@ -94,10 +100,43 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 
+// Double-float number: the unevaluated sum hi + lo of two floats.  A sum of
+// products is formed by compensated dot-product summation (Ogita, Rump and
+// Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26 (2005),
+// algorithm Dot2, extended to double-float factors): every product a b is
+// split without error into p + e by one FMA (e = fma(a.hi, b.hi, -p)), the
+// cross terms a.hi b.lo + a.lo b.hi join e, p enters the running hi by an
+// error-free two-sum, and all error terms gather in lo.  Inside a sum the
+// pair is unnormalised; fin_t renormalises it (|lo| <= ulp(hi) / 2) before it
+// is stored or multiplied again.  The result carries about 48 significant
+// bits, in FP32 arithmetic only.
+struct __align__(8) Df {
+  float hi, lo;
+  Df() = default;
+  __device__ constexpr Df(float h, float l = 0.f) : hi(h), lo(l) {}
+};
+__device__ __forceinline__ Df fma_t(Df a, Df b, Df acc) {
+  const float p = a.hi * b.hi;
+  float e = fmaf(a.hi, b.hi, -p);                  // a.hi b.hi = p + e exactly
+  e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));       // a.lo b.lo is below the pair's precision
+  const float s = acc.hi + p;                      // two-sum: acc.hi + p = s + err exactly
+  const float bv = s - acc.hi;
+  const float err = (acc.hi - (s - bv)) + (p - bv);
+  return Df(s, acc.lo + (err + e));
+}
+__device__ __forceinline__ float fin_t(float v) { return v; }
+__device__ __forceinline__ double fin_t(double v) { return v; }
+__device__ __forceinline__ Df fin_t(Df v) {   // fast two-sum (|hi| >= |lo|)
+  const float h = v.hi + v.lo;
+  return Df(h, v.lo - (h - v.hi));
+}
+__device__ __forceinline__ double to_double(double v) { return v; }
+__device__ __forceinline__ double to_double(Df v) { return (double)v.hi + (double)v.lo; }
+
 // Modes of the tensor kernel.
 constexpr int kTxCgStep = 0;   // FP32: one step of the inner CG (t = A z and the direction epilogue)
 constexpr int kTxApply = 1;    // FP32: y = A x
-constexpr int kTxInit = 2;     // FP64: the refinement's defect d = b - A u and the FP32 CG start
+constexpr int kTxInit = 2;     // FP64 or double-float: the refinement's defect d = b - A u and the FP32 CG start
 constexpr int kTxLayer = 3;    // FP32: y += K (ubar - u) for the stop test (plain stiffness K)
 
 // Dynamic shared memory of the tensor kernel (element type T): the staged
@@ -178,6 +217,9 @@ __global__ void __launch_bounds__(kTileRows, sizeof(T) == 4 ? 3 : 2)
   } else if constexpr (sizeof(T) == 4) {
     cK = d.cK32;
     cM = d.cM32;
+  } else if constexpr (std::is_same<T, Df>::value) {
+    cK = reinterpret_cast<const Df*>(d.cKdf);
+    cM = reinterpret_cast<const Df*>(d.cMdf);
   } else {
     cK = d.cK64;
     cM = d.cM64;
@@ -229,7 +271,8 @@ __global__ void __launch_bounds__(kTileRows, sizeof(T) == 4 ? 3 : 2)
   const int zown = (j - jlo + 2) * nx + i;  // this column in the staged plane
   const T* __restrict__ src;
   if constexpr (MODE == kTxCgStep) src = d.z32;
-  else if constexpr (MODE == kTxInit) src = d.ub;
+  else if constexpr (MODE == kTxInit && std::is_same<T, Df>::value) src = reinterpret_cast<const Df*>(d.ub2);
+  else if constexpr (MODE == kTxInit) src = reinterpret_cast<const T*>(d.ub);
   else if constexpr (MODE == kTxLayer) src = d.dl32;
   else src = xin;
   float beta = 0.f, sc = 1.f;
@@ -291,8 +334,8 @@ __global__ void __launch_bounds__(kTileRows, sizeof(T) == 4 ? 3 : 2)
                 sm = fma_t(cy[b], v, sm);
                 sk = fma_t(cy[5 + b], v, sk);
               }
-              TM[ypad[m]] = sm;
-              TK[ypad[m]] = sk;
+              TM[ypad[m]] = fin_t(sm);
+              TK[ypad[m]] = fin_t(sk);
             }
           }
           if (MODE == kTxCgStep && valid) zc_own = S[st][zown];
@@ -309,8 +352,8 @@ __global__ void __launch_bounds__(kTileRows, sizeof(T) == 4 ? 3 : 2)
           }
         }
         // ring slot u holds plane kk; slot (u + 1 + c) % 5 holds plane kk - 4 + c
-        ph[u] = P;
-        qh[u] = Q;
+        ph[u] = fin_t(P);
+        qh[u] = fin_t(Q);
         zh[u] = zc_own;
         const int k = kk - 2;   // output plane: its neighbours k-2 .. k+2 are in the rings
         if (k >= k0 && valid) {
@@ -335,8 +378,9 @@ __global__ void __launch_bounds__(kTileRows, sizeof(T) == 4 ? 3 : 2)
             const int32_t vr = d.box_vec[row];   // the unknown's vector row (-1: Dirichlet)
             if (!dir && vr >= 0) {
               const double b = d.b[vr];
-              const double dfc = b - t;
-              d.y[vr] = t;
+              const double tv = to_double(t);
+              const double dfc = b - tv;
+              d.y[vr] = tv;
               const float r = (float)dfc;
               const float z = d.dinv32b[row] * r;
               d.r32[row] = r;
@@ -436,6 +480,9 @@ cudaError_t tensor_kernel_setup() {
     e = cudaFuncSetAttribute(k_tensor<double, kTxInit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TxSmem<double, kTxInit>::BYTES);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tensor<Df, kTxInit>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TxSmem<Df, kTxInit>::BYTES);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tensor<float, kTxLayer>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)TxSmem<float, kTxLayer>::BYTES);
   return e;
@@ -455,6 +502,11 @@ cudaError_t launch_tensor_apply32(const DevProblem& d, const float* x, float* y,
 cudaError_t launch_tensor_layer(const DevProblem& d, cudaStream_t s) {
   k_tensor<float, kTxLayer><<<(unsigned)d.n_cta32, kTileRows, TxSmem<float, kTxLayer>::BYTES, s>>>(d, nullptr,
                                                                                                    nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tensor_init_df(const DevProblem& d, cudaStream_t s) {
+  k_tensor<Df, kTxInit><<<(unsigned)d.n_cta32, kTileRows, TxSmem<Df, kTxInit>::BYTES, s>>>(d, nullptr, nullptr);
   return cudaGetLastError();
 }
 

@@ -29,18 +29,20 @@ def _instances():
     return [a, b, c, d]
 
 
-@pytest.mark.parametrize("prec, fp32_op, start", [("fp64", 0, 0), ("mixed", 1, 0), ("mixed", 2, 1), ("mixed", 2, 2)])
+@pytest.mark.parametrize("prec, fp32_op, start",
+                         [("fp64", 0, 0), ("mixed", 1, 0), ("mixed", 2, 1), ("mixed", 2, 2), ("mixed", 2, 3)])
 def test_batch_equals_single_solves(osm, prec, fp32_op, start):
     probs = _instances()
     # the FP32 operator and the refinement's FP64 start are pinned: the
     # autotuner could pick differently for the batch and for a single instance
     kw = dict(prec=prec, inner_rtol=1e-13, max_outer=3000, fp32_operator=fp32_op, fp64_start=start)
     bs = osm.BatchSolver(probs, **kw)
-    phi, iters, rel = bs.solve(rtol=1e-10)
-    assert np.all(rel <= 1e-10)
+    rt = 1e-9 if start == 3 else 1e-10   # the double-float start serves stop tolerances >= 1e-9
+    phi, iters, rel = bs.solve(rtol=rt)
+    assert np.all(rel <= rt)
     for i, q in enumerate(probs):
         one = osm.Solver.from_problem(q, **kw)
-        ph1, n1, r1 = one.solve(rtol=1e-10)
+        ph1, n1, r1 = one.solve(rtol=rt)
         assert iters[i] == n1 and rel[i] == r1, (i, iters[i], n1, rel[i], r1)
         pi = bs.instance_phi(phi, i)
         assert bool((pi == ph1).all()), i

@@ -177,3 +177,39 @@ def test_tensor_batch_equals_single_solves(osm):
 def test_bad_fp32_operator_is_rejected(osm):
     with pytest.raises(osm.OsmError):
         osm.Solver.from_problem(gen.sphere_problem(4, 2, 1.0), prec="mixed", fp32_operator=3)
+
+
+@pytest.mark.parametrize("case", ["sphere16", "uneven"])
+def test_double_float_start_tracks_the_fp64_start(osm, case):
+    """The refinement start in double-float arithmetic (fp64_start 3) against
+    the FP64 one (2), everything else equal: the defects differ by their
+    rounding (about 2^-48 |A| |u| against 2^-53), far below the FP32 inner
+    solve's, so the first stop test agrees to rounding and the Schwarz
+    residual histories stay close; a solve to
+    1e-9 with it reaches the oracle's solution like the FP64 start does; a
+    tighter stop tolerance falls back to the FP64 start and still gets
+    there."""
+    prob = gen.sphere_problem(16, 2, 10.0) if case == "sphere16" else small_uneven()
+    ref = _mono(prob)
+    kw = dict(prec="mixed", mixed_inner_rtol=0.3, inner_rtol=1e-13, max_outer=4000, fp32_operator=2)
+    hist, phis = {}, {}
+    for start in (2, 3):
+        sol = osm.Solver.from_problem(prob, fp64_start=start, **kw)
+        assert sol.info["fp64_start"] == start
+        hist[start] = np.asarray(sol.iterate(30))
+        phi, n, rel = sol.solve(rtol=1e-9)
+        assert rel <= 1e-9
+        phis[start] = phi.cpu().numpy()
+        assert np.linalg.norm(phis[start] - ref) <= 1e-8 * np.linalg.norm(ref), start
+        if start == 3:   # below 1e-9 the FP64 start serves
+            phi, n, rel = sol.solve(rtol=1e-11)
+            assert rel <= 1e-11
+            assert np.linalg.norm(phi.cpu().numpy() - ref) <= 1e-9 * np.linalg.norm(ref)
+            assert sol.info["fp64_start"] == 3
+    # the first stop test sees the same iterate in both runs (the first
+    # defect, b - A 0, is exact): only the start's rounding of A u differs
+    assert abs(hist[3][0] - hist[2][0]) <= 1e-12 * hist[2][0], (hist[3][0], hist[2][0])
+    # afterwards the FP32 inner CG turns any rounding difference in its input
+    # into a different (equally valid) trajectory: the histories stay close
+    assert np.all(np.abs(hist[3] - hist[2]) <= 1e-3 * hist[2]), np.max(np.abs(hist[3] - hist[2]) / hist[2])
+    assert np.linalg.norm(phis[3] - phis[2]) <= 1e-8 * np.linalg.norm(ref)
