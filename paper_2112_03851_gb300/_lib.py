@@ -227,9 +227,6 @@ class Solver:
             msg = L.osm_last_error(h).decode() if h.value else ""
             self.close()
             raise OsmError(st, msg)
-        info = OsmInfo()
-        L.osm_info(h, C.byref(info))
-        self.info = _info_dict(info)
         if tc is not None:
             self.set_transmission(*tc)
         elif p is not None:
@@ -242,6 +239,15 @@ class Solver:
     def from_problem(cls, prob, p=None, tc=None, **opts):
         return cls(prob.xc, prob.yc, prob.zc, prob.drho, prob.cx, prob.cy, prob.cz,
                    p=prob.p if p is None else p, tc=tc, **opts)
+
+    @property
+    def info(self):
+        """osm_info of the handle as it is now: the FP32 operator and the
+        refinement start follow set_transmission / set_robin (a second-order
+        condition moves a tensor-form handle back to the SELL matrix)."""
+        info = OsmInfo()
+        self._check(load().osm_info(self._h, C.byref(info)))
+        return _info_dict(info)
 
     # ------------------------------------------------------------ plumbing
     def _check(self, st, allow=()):
@@ -460,9 +466,6 @@ class BatchSolver(Solver):
             msg = L.osm_last_error(h).decode() if h.value else ""
             self.close()
             raise OsmError(st, msg)
-        info = OsmInfo()
-        L.osm_info(h, C.byref(info))
-        self.info = _info_dict(info)
         self.n_inst = n
         off = np.zeros(n + 1, dtype=np.int64)
         ni = C.c_int32()

@@ -150,6 +150,7 @@ def test_second_order_condition_falls_back_to_sell(osm):
     info = osm._lib.OsmInfo()
     osm.load().osm_info(sol._h, osm._lib.C.byref(info))
     assert info.fp32_operator == 1 and info.fp32_operator_tuned == 2
+    assert sol.info["fp32_operator"] == 1 and sol.info["fp64_start"] == 1   # the binding's view follows too
     phi, n, rel = sol.solve(rtol=1e-10)
     assert rel <= 1e-10 and np.linalg.norm(phi.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
     # unsymmetric zeroth order (q = 0) is back on the tensor form
