@@ -130,6 +130,10 @@ typedef struct {
                                rounding, about 2^-48 |A| |u| per row, stays some 100x
                                below a stop tolerance of 1e-8 on these meshes; use 1 or
                                2 for tolerances below about 1e-10. */
+    int32_t tensor_zchunk;  /* tensor form: z planes per CTA of the tensor-product kernels
+                               (a box's z range is cut into chunks of nearly equal length
+                               up to this).  0 (default): chosen by the autotuner among
+                               8, 16, 32 and 128; 8 .. 128: that length. */
 } osm_opts;
 
 typedef struct {
@@ -173,6 +177,9 @@ typedef struct {
     double start_ms[3];          /* autotuner timings of that step: SELL, FP64 tensor,
                                     double-float tensor (ms, 0 if not run) */
     int64_t box_rows;            /* rows of the box layout of the tensor form (0 if none) */
+    double tensor_ms_zchunk_tail[4];  /* the same timings with one subdomain in eight active (the
+                                    tail of an inner solve); the autotuner keeps the z chunk
+                                    with the smallest sum of both */
 } osm_info_t;
 
 typedef struct {

@@ -41,7 +41,7 @@ class OsmOpts(C.Structure):
     _fields_ = [("prec", C.c_int32), ("inner_rtol", C.c_double), ("mixed_inner_rtol", C.c_double),
                 ("max_outer", C.c_int32), ("max_inner", C.c_int32), ("use_graph", C.c_int32),
                 ("max_seconds", C.c_int32), ("autotune", C.c_int32), ("index16", C.c_int32),
-                ("fp32_operator", C.c_int32), ("fp64_start", C.c_int32)]
+                ("fp32_operator", C.c_int32), ("fp64_start", C.c_int32), ("tensor_zchunk", C.c_int32)]
 
 
 class OsmInfo(C.Structure):
@@ -57,7 +57,8 @@ class OsmInfo(C.Structure):
                 ("fp32_operator", C.c_int32), ("fp32_operator_tuned", C.c_int32),
                 ("tensor_ms_fp32", C.c_double), ("tensor_zchunk", C.c_int32), ("reserved_i", C.c_int32),
                 ("tensor_ms_zchunk", C.c_double * 4), ("fp64_start", C.c_int32), ("reserved_j", C.c_int32),
-                ("start_ms", C.c_double * 3), ("box_rows", C.c_int64)]
+                ("start_ms", C.c_double * 3), ("box_rows", C.c_int64),
+                ("tensor_ms_zchunk_tail", C.c_double * 4)]
 
 
 def _info_dict(info):

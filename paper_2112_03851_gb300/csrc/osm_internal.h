@@ -400,7 +400,9 @@ cudaError_t launch_cg_iteration(const DevProblem& d, cudaStream_t s, unsigned lo
 // The CG-step SpMV kernel alone (fp32: k_cg_spmv_dir32, else k_cg_spmv<double>)
 // and the state that makes it run on every subdomain (profiling only).
 cudaError_t launch_cg_spmv_alone(const DevProblem& d, int fp32, cudaStream_t s);
-cudaError_t launch_profile_state(const DevProblem& d, cudaStream_t s);
+// CG state for timing a CG step alone: every stride-th subdomain active
+// (stride 1: all), beta = 0.5, unit dot-product scaling.
+cudaError_t launch_profile_state(const DevProblem& d, cudaStream_t s, int stride = 1);
 // Assembled nodal load and ||f||^2 partials for the stop test (once per solve).
 cudaError_t launch_load_nodes(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_cg_iteration32(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond);

@@ -517,10 +517,10 @@ __global__ void __launch_bounds__(kTileRows) k_cg_update32(DevProblem d, CgVec<f
 
 // Profiling state: every subdomain active, beta = 1/2 (the full epilogue of
 // k_cg_spmv_dir32 runs), unit dot scale.
-__global__ void k_profile_state(DevProblem d) {
+__global__ void k_profile_state(DevProblem d, int stride) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= d.n_sub) return;
-  d.st.active[s] = 1;
+  d.st.active[s] = s % stride == 0 ? 1 : 0;
   d.st.beta[s] = 0.5;
   d.st.sc[s] = 1.f;
   d.st.isc2[s] = 1.0;
@@ -928,8 +928,8 @@ cudaError_t launch_cg_spmv_alone(const DevProblem& d, int fp32, cudaStream_t s) 
   return cudaGetLastError();
 }
 
-cudaError_t launch_profile_state(const DevProblem& d, cudaStream_t s) {
-  k_profile_state<<<blocks_for(d.n_sub, 256), 256, 0, s>>>(d);
+cudaError_t launch_profile_state(const DevProblem& d, cudaStream_t s, int stride) {
+  k_profile_state<<<blocks_for(d.n_sub, 256), 256, 0, s>>>(d, stride < 1 ? 1 : stride);
   return cudaGetLastError();
 }
 
