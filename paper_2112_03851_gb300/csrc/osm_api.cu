@@ -261,8 +261,47 @@ osm_status upload_problem(osm_ctx* h) {
   OSM_CUDA(h, dalloc(h, &d.inst_done, hp.n_inst));
   OSM_CUDA(h, dalloc(h, &d.inst_iters, hp.n_inst));
   OSM_CUDA(h, dalloc(h, &d.inst_relres, hp.n_inst));
-  OSM_CUDA(h, dalloc(h, &d.rpart, d.n_rblocks));
+  // interface nodes (two or more copies) of each instance and their blocks
+  {
+    std::vector<int32_t> inodes, iblock_inst, inst_iblock0(hp.n_inst + 1, 0);
+    std::vector<int64_t> iblock0;
+    for (int i = 0; i < hp.n_inst; ++i) {
+      inst_iblock0[i] = (int32_t)iblock_inst.size();
+      const size_t first = inodes.size();
+      for (int64_t n = hp.rblock_node0[hp.inst_rblock0[i]]; n < hp.rblock_node0[hp.inst_rblock0[i + 1]]; ++n)
+        if (hp.cp_ptr[n + 1] - hp.cp_ptr[n] >= 2) inodes.push_back((int32_t)n);
+      for (size_t k = first; k < inodes.size(); k += 256) {
+        iblock0.push_back((int64_t)k);
+        iblock_inst.push_back(i);
+      }
+    }
+    inst_iblock0[hp.n_inst] = (int32_t)iblock_inst.size();
+    iblock0.push_back((int64_t)inodes.size());
+    d.n_iblocks = (int64_t)iblock_inst.size();
+    int32_t *din, *dii, *dib;
+    int64_t* di0;
+    OSM_CUDA(h, upload(h, &din, inodes));
+    OSM_CUDA(h, upload(h, &di0, iblock0));
+    OSM_CUDA(h, upload(h, &dii, iblock_inst));
+    OSM_CUDA(h, upload(h, &dib, inst_iblock0));
+    d.inodes = din; d.iblock0 = di0; d.iblock_inst = dii; d.inst_iblock0 = dib;
+  }
+  OSM_CUDA(h, dalloc(h, &d.rpart, std::max<int64_t>(1, d.n_iblocks)));
   OSM_CUDA(h, dalloc(h, &d.rpart2, d.n_rblocks));
+  // the stop test's row-wise part: single-copy row flags, per-tile partials,
+  // and each instance's tile range (its subdomains are consecutive)
+  OSM_CUDA(h, dalloc(h, &d.tpart, hp.n_tiles));
+  {
+    std::vector<int64_t> it0(hp.n_inst + 1, hp.n_tiles);
+    for (int s = hp.nsub - 1; s >= 0; --s) it0[hp.sub_inst[s]] = hp.sub[s].tile0;
+    int64_t* dit0;
+    OSM_CUDA(h, upload(h, &dit0, it0));
+    d.inst_tile0 = dit0;
+    uint8_t* single;
+    OSM_CUDA(h, dalloc(h, &single, nv));
+    OSM_CUDA(h, launch_mark_single(d, single, h->stream));
+    d.row_single = single;
+  }
   OSM_CUDA(h, dalloc(h, &d.fg, hp.n_nodes));
   OSM_CUDA(h, dalloc(h, &d.hist, h->opts.max_outer > 0 ? h->opts.max_outer : 1));
   OSM_CUDA(h, dalloc(h, &d.ctl, 1));
@@ -871,6 +910,7 @@ osm_status run_iterations(osm_ctx* h, double rtol, int max_outer) {
       if (h->ctl_host->running == 0 || h->ctl_host->stop) break;
     }
   }
+  OSM_CUDA(h, launch_phi(h->d, h->stream));   // phi = ubar of the final iterate of every instance
   OSM_CUDA(h, cudaMemcpyAsync(h->ctl_host, h->d.ctl, sizeof(DevCtl), cudaMemcpyDeviceToHost, h->stream));
   OSM_CUDA(h, cudaStreamSynchronize(h->stream));
   return OSM_OK;
@@ -1314,16 +1354,17 @@ osm_status osm_stats(osm_handle h, osm_stats_t* o) {
     const int64_t per_outer = 3 + mixed + faces + 3;
     o->n_launches = 1 + per_outer * c.n_outer + 5 * (int64_t)c.total_inner;
   } else {
-    // solve: once the nodal load, the first RHS gather and CG start; per
-    // Schwarz iteration the CG finaliser, FP64 correction (mixed), exchange
-    // (if any face), the next RHS gather and CG start, average, interface
-    // layer (if any; on the tensor form the transmission correction and the
-    // FP32 tensor kernel), residual partials, residual finaliser; per CG step
-    // SpMV (+ direction epilogue in FP32) and update (+ the step's finish),
-    // plus the FP64 direction
+    // solve: once the nodal load, the first RHS gather and CG start, and at
+    // the end phi; per Schwarz iteration the CG finaliser, FP64 correction
+    // (mixed), exchange (if any face), the next RHS gather and CG start,
+    // average, interface layer (if any; on the tensor form the transmission
+    // correction and the FP32 tensor kernel), residual partials of the
+    // interface nodes and of the single-copy rows, residual finaliser; per CG
+    // step SpMV (+ direction epilogue in FP32) and update (+ the step's
+    // finish), plus the FP64 direction
     const int64_t layer = h->d.dl32 ? 1 + (h->hp.irow.empty() ? 0 : 1) : (h->hp.li_row.empty() ? 0 : 1);
-    const int64_t per_outer = 1 + mixed + faces + 2 + 1 + layer + 2;
-    o->n_launches = 3 + per_outer * c.n_outer + (mixed ? 2 : 3) * (int64_t)c.total_inner;
+    const int64_t per_outer = 1 + mixed + faces + 2 + 1 + layer + 3;
+    o->n_launches = 4 + per_outer * c.n_outer + (mixed ? 2 : 3) * (int64_t)c.total_inner;
   }
   o->relres = c.relres;
   o->status = c.status;

@@ -276,6 +276,18 @@ struct DevProblem {
   double* phi;          // internal full-grid output
   double* rpart;        // stop-test partials of ||r||^2 (per residual block)
   double* rpart2;       // ... of ||f||^2 (written once per solve by k_load_nodes)
+  double* tpart;        // stop-test partials of ||r||^2 over the single-copy rows, one per tile
+  // interface nodes (two or more copies) of every instance in node order, in
+  // blocks of up to 256 of one instance: [iblock0[b], iblock0[b+1]) of
+  // inodes, instance iblock_inst[b]; inst_iblock0 (n_inst + 1) is each
+  // instance's first block.  The per-iteration averaging and the interface
+  // part of the residual run over these (rpart: one partial per block).
+  const int32_t* inodes;
+  const int64_t* iblock0;
+  const int32_t *iblock_inst, *inst_iblock0;
+  int64_t n_iblocks;
+  const uint8_t* row_single;  // 1: the vector row's node has no other copy (subdomain interior)
+  const int64_t* inst_tile0;  // n_inst + 1: first tile of each instance
   double* fg;           // assembled load per node (full grid), set per solve
   int64_t n_rblocks;
   double* hist;         // residual history (max_outer)
@@ -415,6 +427,9 @@ cudaError_t launch_tensor_coef(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_tensor_dir32(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_tensor_apply32(const DevProblem& d, const float* x, float* y, cudaStream_t s);
 cudaError_t launch_tensor_init64(const DevProblem& d, cudaStream_t s);
+// setup: flag the vector rows whose node has one copy; end of a call: phi
+cudaError_t launch_mark_single(const DevProblem& d, uint8_t* single, cudaStream_t s);
+cudaError_t launch_phi(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_tensor_init_df(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_box_mirror(const DevProblem& d, cudaStream_t s);
 cudaError_t launch_tensor_layer(const DevProblem& d, cudaStream_t s);

@@ -670,21 +670,20 @@ __global__ void k_exchange(DevProblem d) {
   *lts = fma(pp, mus, qq * sus) - old_st;
 }
 
-// Stop test, step 1: ubar = average of the copies of each node; phi = ubar
-// on the full grid; w = ubar scattered back to every copy.
+// Stop test, step 1, at the interface nodes (two or more copies): ubar =
+// average of the copies, scattered back to every copy (w) and, on handles
+// with a box layout, ubar - u for the tensor layer.  A node with one copy
+// has ubar = u, so ubar - u = 0 there (dl32 stays zero) and its w is never
+// read; phi is formed once per call by k_phi.
 __global__ void k_average(DevProblem d) {
   const int b = blockIdx.x;
-  if (d.inst_done[d.rblock_inst[b]]) return;  // a finished instance keeps its phi
-  for (int64_t n = d.rblock_node0[b] + threadIdx.x; n < d.rblock_node0[b + 1]; n += blockDim.x) {
+  if (d.inst_done[d.iblock_inst[b]]) return;
+  for (int64_t k = d.iblock0[b] + threadIdx.x; k < d.iblock0[b + 1]; k += blockDim.x) {
+    const int32_t n = d.inodes[k];
     const int32_t c0 = d.cp_ptr[n], c1 = d.cp_ptr[n + 1];
-    if (c0 == c1) {
-      d.phi[n] = 0.0;
-      continue;
-    }
     double s = 0.0;
     for (int32_t c = c0; c < c1; ++c) s += d.x[d.cp_idx[c]];
     const double ub = copy_mean(s, c1 - c0);
-    d.phi[n] = ub;
     for (int32_t c = c0; c < c1; ++c) {
       const int32_t r = d.cp_idx[c];
       d.w[r] = ub;
@@ -743,15 +742,19 @@ __global__ void __launch_bounds__(256) k_stop_layer(DevProblem d) {
   if (k < d.n_lrow && sub == 0) d.y[d.li_row[k]] += acc;
 }
 
-// Stop test, step 2: r = sum_copies f - sum_copies K_i ubar per node, and
-// the per-block partials of ||r||^2 and ||f||^2 (no tickets: the single-block
-// k_residual_fin adds them).
+// Stop test, step 2, at the interface nodes: r = sum_copies f -
+// sum_copies K_i ubar per node and the per-block partials of ||r||^2 (no
+// tickets: the single-block k_residual_fin adds them to those of
+// k_residual_rows).  A node with one copy is the single-copy row's, r = f -
+// y there, and k_residual_rows streams those; a node without copies
+// (Dirichlet) has r = 0.
 __global__ void __launch_bounds__(256) k_residual(DevProblem d) {
   __shared__ double sm[1][256];
   const int b = blockIdx.x;
   double v[1] = {0.0};
-  if (!d.inst_done[d.rblock_inst[b]]) {
-    for (int64_t n = d.rblock_node0[b] + threadIdx.x; n < d.rblock_node0[b + 1]; n += blockDim.x) {
+  if (!d.inst_done[d.iblock_inst[b]]) {
+    for (int64_t k = d.iblock0[b] + threadIdx.x; k < d.iblock0[b + 1]; k += blockDim.x) {
+      const int32_t n = d.inodes[k];
       const int32_t c0 = d.cp_ptr[n], c1 = d.cp_ptr[n + 1];
       double ku = 0.0;
       for (int32_t c = c0; c < c1; ++c) ku += d.y[d.cp_idx[c]];
@@ -761,6 +764,52 @@ __global__ void __launch_bounds__(256) k_residual(DevProblem d) {
   }
   block_sum_d<1, 256>(v, sm);
   if (threadIdx.x == 0) d.rpart[b] = v[0];
+}
+
+// Stop test, step 2 on the single-copy rows (every other row): r = f - y
+// on the vector row itself, read as contiguous streams.  One warp per tile
+// of 256 rows (8 rows per lane, no block barrier) and its partial of
+// ||r||^2 per tile.  Padding rows have f = y = 0.
+__global__ void __launch_bounds__(kTileRows) k_residual_rows(DevProblem d) {
+  const int64_t tile = blockIdx.x * (int64_t)kTileSlices + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (tile >= d.n_tiles) return;
+  if (d.inst_done[d.sub_inst[d.tile_sub[tile]]]) return;   // k_residual_fin skips the instance
+  double v = 0.0;
+#pragma unroll
+  for (int k = 0; k < kTileRows / 32; ++k) {
+    const int64_t row = tile * kTileRows + k * 32 + lane;
+    if (d.row_single[row]) {
+      const double r = d.f[row] - d.y[row];
+      v = fma(r, r, v);
+    }
+  }
+  v = warp_sum(v);
+  if (lane == 0) d.tpart[tile] = v;
+}
+
+// Marks the vector rows whose node has exactly one copy (setup).
+__global__ void k_mark_single(DevProblem d, uint8_t* single) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < d.n_nodes;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c0 = d.cp_ptr[n], c1 = d.cp_ptr[n + 1];
+    if (c1 - c0 == 1) single[d.cp_idx[c0]] = 1;
+  }
+}
+
+// phi = the average of the copies of every node (0 on the Dirichlet boundary,
+// where a node has none), once at the end of a solve or iterate call.  An
+// instance that finished earlier in the call has a frozen iterate (its
+// subdomain solves add nothing and its exchange stops), so its phi is that of
+// its last stop test.
+__global__ void k_phi(DevProblem d) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < d.n_nodes;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c0 = d.cp_ptr[n], c1 = d.cp_ptr[n + 1];
+    double s = 0.0;
+    for (int32_t c = c0; c < c1; ++c) s += d.x[d.cp_idx[c]];
+    d.phi[n] = c0 == c1 ? 0.0 : copy_mean(s, c1 - c0);
+  }
 }
 
 // Start of a solve: the assembled load f_n = sum over the copies of each
@@ -790,19 +839,16 @@ __global__ void __launch_bounds__(kResFinThreads) k_residual_fin(DevProblem d, u
   const int n_outer = d.ctl->n_outer;
   for (int inst = 0; inst < d.n_inst; ++inst) {
     if (d.inst_done[inst]) continue;   // uniform across the block
+    // ||f||^2: one partial per node block; ||r||^2: one per interface-node
+    // block and one per tile of single-copy rows
     const int b0 = d.inst_rblock0[inst], nb = d.inst_rblock0[inst + 1] - b0;
+    const int i0 = d.inst_iblock0[inst], ni = d.inst_iblock0[inst + 1] - i0;
     double u[2] = {0.0, 0.0}, w[2] = {0.0, 0.0};
-    int k = threadIdx.x;
-    for (; k + (int)blockDim.x < nb; k += 2 * blockDim.x) {
-      u[0] += __ldcg(d.rpart + b0 + k);
-      u[1] += __ldcg(d.rpart2 + b0 + k);
-      w[0] += __ldcg(d.rpart + b0 + k + blockDim.x);
-      w[1] += __ldcg(d.rpart2 + b0 + k + blockDim.x);
-    }
-    if (k < nb) {
-      u[0] += __ldcg(d.rpart + b0 + k);
-      u[1] += __ldcg(d.rpart2 + b0 + k);
-    }
+    for (int k = threadIdx.x; k < nb; k += blockDim.x) u[1] += __ldcg(d.rpart2 + b0 + k);
+    for (int k = threadIdx.x; k < ni; k += blockDim.x) u[0] += __ldcg(d.rpart + i0 + k);
+    // the single-copy rows' partials, one per tile of the instance
+    for (int64_t t = d.inst_tile0[inst] + threadIdx.x; t < d.inst_tile0[inst + 1]; t += blockDim.x)
+      w[0] += __ldcg(d.tpart + t);
     u[0] += w[0];
     u[1] += w[1];
     block_sum<2, kResFinThreads / 32>(u, sm);
@@ -983,7 +1029,7 @@ cudaError_t launch_fin_init(const DevProblem& d, cudaStream_t s, unsigned long l
 }
 
 cudaError_t launch_stop_test(const DevProblem& d, cudaStream_t s, unsigned long long cond, int use_cond) {
-  k_average<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
+  if (d.n_iblocks) k_average<<<(unsigned)d.n_iblocks, 256, 0, s>>>(d);
   if (d.dl32) {   // box layout: the transmission part in FP64, K (ubar - u) by the FP32 tensor kernel
     if (d.n_irow) k_face_correct<<<blocks_for(d.n_irow, 256), 256, 0, s>>>(d, d.x, d.y);
     cudaError_t e = launch_tensor_layer(d, s);
@@ -991,8 +1037,19 @@ cudaError_t launch_stop_test(const DevProblem& d, cudaStream_t s, unsigned long 
   } else if (d.n_lrow) {
     k_stop_layer<<<blocks_for((int64_t)d.n_lrow * kLayerLanes, 256), 256, 0, s>>>(d);
   }
-  k_residual<<<(unsigned)d.n_rblocks, 256, 0, s>>>(d);
+  if (d.n_iblocks) k_residual<<<(unsigned)d.n_iblocks, 256, 0, s>>>(d);
+  k_residual_rows<<<(unsigned)((d.n_tiles + kTileSlices - 1) / kTileSlices), kTileRows, 0, s>>>(d);
   k_residual_fin<<<1, kResFinThreads, 0, s>>>(d, cond, use_cond);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mark_single(const DevProblem& d, uint8_t* single, cudaStream_t s) {
+  k_mark_single<<<kNodeBlocks, 256, 0, s>>>(d, single);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phi(const DevProblem& d, cudaStream_t s) {
+  k_phi<<<kNodeBlocks, 256, 0, s>>>(d);
   return cudaGetLastError();
 }
 
