@@ -61,3 +61,16 @@ def test_solve_level_fraction_counts_the_rows_processed():
     r = bench._solve_hbm(sol, "mixed", m)
     want = (20 + bench.UPD32_BYTES_PER_ROW) * 1e9 + bench.MIXED_OUTER_BYTES_PER_ROW * 2_300_000 * 100
     assert abs(r["bytes_per_solve"] - want) <= 1 and "tensor" in r["counted"]
+
+
+def test_double_float_start_roofline_counts_fp32_operations():
+    """The double-float refinement start is reported against the measured
+    FP32 rate: DF_OPS_PER_ROW FP32 operations per box row (12 per compensated
+    multiply-add, 3 per renormalisation of the four intermediate sums)."""
+    assert bench.DF_OPS_PER_ROW == 35 * 12 + 4 * 3
+    sol = _FakeSolver()
+    sol.info = dict(sol.info, fp32_operator=2, fp64_start=3, box_rows=1_000_000)
+    r = bench._roofline_fp64_start(sol)
+    assert r["bound"] == "alu" and r["unit"] == "G FP32 ops/s" and r["peak"] == bench.FP32_OPS_PEAK_G
+    want = bench.DF_OPS_PER_ROW * 1e6 / 0.25e-3 / 1e9
+    assert abs(r["achieved"] - want) < 0.1 and abs(r["frac"] - want / bench.FP32_OPS_PEAK_G) < 1e-4
